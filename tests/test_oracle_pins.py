@@ -1,0 +1,337 @@
+"""Pins for the FP64 CPU oracle: each check ties it to something other than
+itself (symbolic derivatives, conservation laws, polynomial exactness,
+closed forms, the analytic Kepler orbit), so that a dropped term, a wrong
+sign or coefficient, or a transposed operand fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import nb_inputs as ni
+import oracle as O
+
+
+# --------------------------------------------------------------- pair terms
+
+def _sympy_pair(xi, vi, ai, xj, vj, aj, mj, eps):
+    """acc, jerk, snap of a softened pair by symbolic differentiation of
+    A(tau) = m r(tau) / (|r(tau)|^2 + eps^2)^(3/2) along
+    r(tau) = dx + dv tau + da tau^2 / 2 (sympy, 40 digits)."""
+    sp = pytest.importorskip("sympy")
+    tau = sp.Symbol("tau")
+    R = [sp.Rational(float(xj[k])) - sp.Rational(float(xi[k])) for k in range(3)]
+    V = [sp.Rational(float(vj[k])) - sp.Rational(float(vi[k])) for k in range(3)]
+    Acc = [sp.Rational(float(aj[k])) - sp.Rational(float(ai[k])) for k in range(3)]
+    r = [R[k] + V[k] * tau + Acc[k] * tau ** 2 / 2 for k in range(3)]
+    e2 = sp.Rational(float(eps)) ** 2
+    den = (r[0] ** 2 + r[1] ** 2 + r[2] ** 2 + e2) ** sp.Rational(3, 2)
+    m = sp.Rational(float(mj))
+    out = []
+    for order in range(3):
+        out.append(np.array([float(sp.diff(m * r[k] / den, tau, order).subs(tau, 0).evalf(40))
+                             for k in range(3)]))
+    return out
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_pair_matches_symbolic_derivatives(seed):
+    s = ni.random_state(6, seed)
+    xi, vi, ai, xj, vj, aj = s
+    mj, eps = 0.37, 0.05
+    got = O.pair(xi, vi, ai, xj, vj, aj, mj, eps)
+    ref = _sympy_pair(xi, vi, ai, xj, vj, aj, mj, eps)
+    for g, r in zip(got, ref):
+        np.testing.assert_allclose(g, r, rtol=1e-13, atol=1e-13 * np.abs(r).max())
+
+
+def test_pair_self_term_is_zero_and_antisymmetric():
+    s = ni.random_state(6, 11)
+    xi, vi, ai, xj, vj, aj = s
+    for q in O.pair(xi, vi, ai, xi, vi, ai, 1.0, 1e-4):
+        assert np.all(q == 0.0)
+    mi, mj = 0.3, 0.7
+    f_ij = O.pair(xi, vi, ai, xj, vj, aj, mj, 0.01)
+    f_ji = O.pair(xj, vj, aj, xi, vi, ai, mi, 0.01)
+    for a, b in zip(f_ij, f_ji):
+        np.testing.assert_allclose(mi * a, -mj * b, rtol=1e-14, atol=1e-15)
+
+
+# ------------------------------------------------------------ evaluation sum
+
+def test_newton_third_law_for_acc_jerk_snap():
+    m, x, v = ni.plummer(256, 5, imf="salpeter")
+    a = ni.random_state(256, 6)
+    acc, jrk, snp = O.evaluate(m, x, v, a, 1e-4)
+    for q in (acc, jrk, snp):
+        tot = (m[:, None] * q).sum(axis=0)
+        scale = (m[:, None] * np.abs(q)).sum()
+        assert np.all(np.abs(tot) < 1e-13 * scale)
+
+
+def test_evaluate_equals_sum_of_pairs_and_skips_self():
+    m, x, v = ni.plummer(9, 3)
+    a = ni.random_state(9, 4)
+    act = np.array([0, 4, 8], dtype=np.int32)
+    acc, jrk, snp = O.evaluate(m, x, v, a, 1e-3, act)
+    for k, i in enumerate(act):
+        tot = [np.zeros(3) for _ in range(3)]
+        for j in range(9):
+            if j != i:
+                for q, t in zip(O.pair(x[i], v[i], a[i], x[j], v[j], a[j], m[j], 1e-3), tot):
+                    t += q
+        np.testing.assert_allclose(acc[k], tot[0], rtol=1e-13)
+        np.testing.assert_allclose(jrk[k], tot[1], rtol=1e-13)
+        np.testing.assert_allclose(snp[k], tot[2], rtol=1e-13)
+
+
+def test_jerk_and_snap_are_time_derivatives_of_acc():
+    """Along x_k(tau) = x_k + v_k tau + a_k tau^2 / 2 for every particle,
+    jerk_i = d acc_i / d tau and snap_i = d^2 acc_i / d tau^2 at tau = 0
+    (5-point central differences, h = 2^-10)."""
+    n = 48
+    m, x, v = ni.plummer(n, 7)
+    a0, _, _ = O.evaluate(m, x, v, np.zeros((n, 3)), 1e-2)
+    acc, jrk, snp = O.evaluate(m, x, v, a0, 1e-2)
+    h = 2.0 ** -10
+
+    def acc_at(tau):
+        return O.evaluate(m, x + v * tau + a0 * tau * tau / 2, v, a0, 1e-2)[0]
+
+    Am2, Am1, A0, Ap1, Ap2 = (acc_at(k * h) for k in (-2, -1, 0, 1, 2))
+    d1 = (Am2 - 8 * Am1 + 8 * Ap1 - Ap2) / (12 * h)
+    d2 = (-Am2 + 16 * Am1 - 30 * A0 + 16 * Ap1 - Ap2) / (12 * h * h)
+    np.testing.assert_allclose(A0, acc, rtol=0, atol=0)
+    for got, fd in ((jrk, d1), (snp, d2)):
+        err = np.abs(got - fd).max(axis=1) / np.linalg.norm(got, axis=1)
+        assert err.max() < 1e-6, err.max()
+
+
+# ------------------------------------------------------------- polynomials
+
+def _poly_state(coef, t):
+    """value and first 5 derivatives of the vector polynomial sum coef[k] t^k."""
+    out = []
+    c = [np.polynomial.Polynomial(coef[:, d]) for d in range(3)]
+    for order in range(8):
+        out.append(np.array([p.deriv(order)(t) if order else p(t) for p in c]))
+    return out
+
+
+def test_predictor_exact_for_quintic_trajectories():
+    rng_coef = ni.random_state(6, 21)
+    ti = np.array([0.25, 0.5])
+    t = 0.75
+    xs, vs, as_, js, ss, cs = [], [], [], [], [], []
+    for k in range(2):
+        st = _poly_state(rng_coef * (k + 1), ti[k])
+        for lst, q in zip((xs, vs, as_, js, ss, cs), st[:6]):
+            lst.append(q)
+    xp, vp, ap = O.predict(t, ti, *(np.array(q) for q in (xs, vs, as_, js, ss, cs)))
+    for k in range(2):
+        st = _poly_state(rng_coef * (k + 1), t)
+        np.testing.assert_allclose(xp[k], st[0], rtol=1e-14, atol=1e-14)
+        np.testing.assert_allclose(vp[k], st[1], rtol=1e-14, atol=1e-14)
+        np.testing.assert_allclose(ap[k], st[2], rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [31, 32])
+def test_corrector_exact_for_degree6_positions(seed):
+    coef = ni.random_state(7, seed)
+    h = 0.125
+    s0 = _poly_state(coef, 0.0)
+    s1 = _poly_state(coef, h)
+    x1, v1 = O.correct(h, s0[0], s0[1], s0[2], s0[3], s0[4], s1[2], s1[3], s1[4])
+    np.testing.assert_allclose(v1, s1[1], rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(x1, s1[0], rtol=1e-14, atol=1e-14)
+
+
+def test_corrector_velocity_exact_for_degree7_and_position_not():
+    coef = np.zeros((8, 3))
+    coef[7] = [1.0, -2.0, 0.5]
+    h = 0.5
+    s0 = _poly_state(coef, 0.0)
+    s1 = _poly_state(coef, h)
+    x1, v1 = O.correct(h, s0[0], s0[1], s0[2], s0[3], s0[4], s1[2], s1[3], s1[4])
+    np.testing.assert_allclose(v1, s1[1], rtol=1e-14, atol=1e-14)
+    # the position quadrature integrates v = 7 t^6 with an h^7 error term
+    assert np.all(np.abs(x1 - s1[0]) > 1e-6 * np.abs(s1[0]))
+
+
+@pytest.mark.parametrize("seed,h", [(41, 0.125), (42, 0.5), (43, 1.0), (44, 2.0 ** -10)])
+def test_interpolation_exact_for_quintic_acceleration(seed, h):
+    """Exact for a(t) of degree 5.  The k-th derivative is recovered from
+    differences of O(|a|) values divided by h^k, so rounding alone bounds its
+    accuracy by about eps_mach |a| / h^k; the tolerance follows that."""
+    coef = np.zeros((8, 3))
+    coef[2:8] = ni.random_state(6, seed)  # x of degree 7 -> a of degree 5
+    s0 = _poly_state(coef, 0.0)
+    s1 = _poly_state(coef, h)
+    c1, d1, e1 = O.interpolate(h, s0[2], s0[3], s0[4], s1[2], s1[3], s1[4])
+    scale = np.abs(np.concatenate([s0[2], s1[2]])).max()
+    for k, (got, ref) in zip((3, 4, 5), ((c1, s1[5]), (d1, s1[6]), (e1, s1[7]))):
+        tol = 1e-13 * np.abs(ref).max() + 1e3 * 2.2e-16 * scale / h ** k
+        assert np.abs(got - ref).max() < tol, (k, np.abs(got - ref).max(), tol)
+
+
+# --------------------------------------------------------------- time steps
+
+def test_aarseth_criterion_on_circular_motion():
+    """x = R (cos wt, sin wt, 0): |a^(k)| = R w^(k+2), so A1 = 2 R w^3,
+    A4 = 2 R w^6 and the 6th-order criterion gives exactly eta / w."""
+    R, w, t, eta = 1.7, 3.0, 0.3, 0.4
+
+    def deriv(k):
+        ph = w * t + k * math.pi / 2
+        return R * w ** k * np.array([math.cos(ph), math.sin(ph), 0.0])
+
+    a, j, s, c, d, e = (deriv(k) for k in range(2, 8))
+    assert O.dt_crit(eta, a, j, s, c, d, e) == pytest.approx(eta / w, rel=1e-14)
+
+
+def test_initial_step():
+    a = np.array([2.0, 0, 0])
+    j = np.array([0, 4.0, 0])
+    s = np.array([0, 0, 1.0])
+    assert O.dt_initial(0.01, a, j, s) == pytest.approx(0.01 * 0.5, rel=1e-15)
+    s = np.array([0, 0, 32.0])
+    assert O.dt_initial(0.01, a, j, s) == pytest.approx(0.01 * 0.25, rel=1e-15)
+
+
+@pytest.mark.parametrize("crit,old,t1,want,hit", [
+    (0.3, -1, 0.0, 0.125, False),          # clamp to dt_max
+    (0.001, -1, 0.0, 2.0 ** -10, False),   # largest power of two below
+    (2.0 ** -7, -1, 0.0, 2.0 ** -7, False),  # exact power of two is kept
+    (1e-9, -1, 0.0, 2.0 ** -20, True),     # floor
+    (float("nan"), 2.0 ** -5, 0.0, 2.0 ** -20, True),
+    (1.0, 2.0 ** -10, 3 * 2.0 ** -10, 2.0 ** -10, False),  # t1 not commensurate
+    (1.0, 2.0 ** -10, 4 * 2.0 ** -10, 2.0 ** -9, False),   # at most doubled
+    (2.0 ** -12 * 1.5, 2.0 ** -5, 0.5, 2.0 ** -12, False),  # any decrease allowed
+])
+def test_quantise_table(crit, old, t1, want, hit):
+    got, h = O.dt_quantise(crit, old, t1)
+    assert got == want and h == hit
+
+
+# --------------------------------------------------------------- diagnostics
+
+def test_energy_two_body_closed_form_and_plummer_virial():
+    m = np.array([0.25, 0.75])
+    x = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0]])
+    v = np.array([[1.0, 0.0, 0.0], [0.0, 2.0, 0.0]])
+    ek, ep = O.energy(m, x, v, 0.0)
+    assert ek == pytest.approx(0.5 * 0.25 + 0.5 * 0.75 * 4.0, rel=1e-15)
+    assert ep == pytest.approx(-0.25 * 0.75 / 5.0, rel=1e-15)
+    m, x, v = ni.plummer(1024, 1)
+    ek, ep = O.energy(m, x, v, 1e-4)
+    assert abs(ek + ep + 0.25) < 0.02 and abs(ek / -ep - 0.5) < 0.03
+
+
+def test_angular_momentum_two_body():
+    m = np.array([1.0, 2.0])
+    x = np.array([[1.0, 0, 0], [0, 1.0, 0]])
+    v = np.array([[0, 1.0, 0], [0, 0, 3.0]])
+    L, la = O.angmom(m, x, v)
+    np.testing.assert_allclose(L, [6.0, 0.0, 1.0])
+    assert la == pytest.approx(7.0)
+
+
+# ------------------------------------------------------------------- Kepler
+
+def kepler_state(t, m1=0.5, m2=0.5, a=1.0, e=0.5):
+    """Two bodies on an ellipse (G = 1), pericentre at t = 0, analytic."""
+    mu = m1 + m2
+    n = math.sqrt(mu / a ** 3)
+    M = n * t
+    E = M
+    for _ in range(60):
+        E -= (E - e * math.sin(E) - M) / (1 - e * math.cos(E))
+    dE = n / (1 - e * math.cos(E))
+    b = a * math.sqrt(1 - e * e)
+    r = np.array([a * (math.cos(E) - e), b * math.sin(E), 0.0])
+    u = np.array([-a * math.sin(E) * dE, b * math.cos(E) * dE, 0.0])
+    x = np.array([-m2 / mu * r, m1 / mu * r])
+    v = np.array([-m2 / mu * u, m1 / mu * u])
+    return np.array([m1, m2]), x, v
+
+
+def _kepler_error(dt, T):
+    m, x, v = kepler_state(0.0)
+    s = O.System(m, x, v, 1e-12, dt_shared=dt, dt_max=dt)
+    s.run_until(T)
+    st = s.state()
+    _, xr, vr = kepler_state(T)
+    return np.abs(st["x"] - xr).max()
+
+
+def test_kepler_matches_analytic_orbit_with_sixth_order_convergence():
+    T = 2.0
+    errs = [_kepler_error(2.0 ** -k, T) for k in (5, 6, 7)]
+    assert errs[2] < 1e-9
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    for p in orders:
+        assert 5.5 < p < 6.6, orders
+
+
+def test_kepler_energy_over_an_orbit():
+    m, x, v = kepler_state(0.0)
+    s = O.System(m, x, v, 1e-12, dt_shared=2.0 ** -10, dt_max=2.0 ** -10)
+    E0 = sum(O.energy(m, x, v, 1e-12))
+    s.run_until(8.0)
+    st = s.state()
+    E1 = sum(O.energy(m, st["x"], st["v"], 1e-12))
+    assert abs((E1 - E0) / E0) < 1e-12
+
+
+def test_kepler_block_steps_follow_analytic_orbit():
+    m, x, v = kepler_state(0.0)
+    s = O.System(m, x, v, 1e-12, eta=0.1)
+    s.run_until(2.0)
+    st = s.state()
+    _, xr, _ = kepler_state(2.0)
+    assert np.abs(st["x"] - xr).max() < 1e-7
+
+
+# ------------------------------------------------------------ block stepping
+
+def test_block_step_invariants_and_plummer_energy():
+    m, x, v = ni.plummer(1024, 1)
+    eps = 1e-4
+    E0 = sum(O.energy(m, x, v, eps))
+    s = O.System(m, x, v, eps)
+    steps, (lt, ln, lh) = s.run_until(0.125, log_cap=100000)
+    assert steps == lt.size and np.all(ln >= 1) and np.all(np.diff(lt) > 0)
+    st = s.state()
+    dt = st["dt"]
+    assert np.all(st["t"] == 0.125)
+    k = np.log2(dt)
+    assert np.all(k == np.round(k)) and dt.min() >= 2.0 ** -20 and dt.max() <= 0.125
+    assert np.all(np.mod(st["t"], dt) == 0.0)
+    E1 = sum(O.energy(m, st["x"], st["v"], eps))
+    assert abs((E1 - E0) / E0) < 1e-9
+
+
+def test_shared_mode_activates_everyone_and_hash_is_sum_of_mixes():
+    m, x, v = ni.plummer(32, 2)
+    s = O.System(m, x, v, 1e-3, dt_shared=2.0 ** -8)
+    t, na, h = s.step()
+    assert t == 2.0 ** -8 and na == 32
+    assert h == O.set_hash(range(32))
+
+
+def test_replay_of_own_log_reproduces_state():
+    m, x, v = ni.plummer(64, 9)
+    a = O.System(m, x, v, 1e-3)
+    b = O.System(m, x, v, 1e-3)
+    tn, sets = [], []
+    for _ in range(12):
+        before = a.state()
+        t, na, h = a.step()
+        due = np.nonzero(before["t"] + before["dt"] == t)[0]
+        assert due.size == na and O.set_hash(due) == h
+        tn.append(t)
+        sets.append(due)
+    b.replay(tn, sets)
+    sa, sb = a.state(), b.state()
+    for k in ("x", "v", "a", "j", "s", "c", "t"):
+        np.testing.assert_array_equal(sa[k], sb[k])

@@ -242,6 +242,8 @@ double orc_dt_quantise(double dt_crit, double dt_old, double t1, double dt_min,
     if (!(dt_crit >= dt_min)) {         /* also catches NaN */
         *floor_hit = 1;
         p = dt_min;
+    } else if (isinf(dt_crit)) {        /* no bound from the criterion */
+        p = dt_max;
     } else {
         int ex;
         frexp(dt_crit, &ex);            /* dt_crit = f 2^ex, 0.5 <= f < 1 */

@@ -200,6 +200,7 @@ def test_initial_step():
 
 @pytest.mark.parametrize("crit,old,t1,want,hit", [
     (0.3, -1, 0.0, 0.125, False),          # clamp to dt_max
+    (float("inf"), -1, 0.0, 0.125, False),  # unbounded criterion -> dt_max
     (0.001, -1, 0.0, 2.0 ** -10, False),   # largest power of two below
     (2.0 ** -7, -1, 0.0, 2.0 ** -7, False),  # exact power of two is kept
     (1e-9, -1, 0.0, 2.0 ** -20, True),     # floor

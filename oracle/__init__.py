@@ -63,6 +63,8 @@ def lib():
             L.orc_pair.argtypes = [_d] * 6 + [C.c_double, C.c_double, _d, _d, _d]
             L.orc_evaluate.argtypes = [C.c_int64, _d, _d, _d, _d, C.c_double, C.c_int64,
                                        _i32, _d, _d, _d]
+            L.orc_evaluate_kappa.argtypes = [C.c_int64, _d, _d, _d, _d, C.c_double, C.c_int64,
+                                             _i32, _d, _d, _d]
             L.orc_predict.argtypes = [C.c_int64, C.c_double] + [_d] * 10
             L.orc_correct.argtypes = [C.c_double] + [_d] * 10
             L.orc_interpolate.argtypes = [C.c_double] + [_d] * 9
@@ -122,6 +124,19 @@ def evaluate(m, x, v, a, eps, active=None):
     out = [np.zeros((act.size, 3)) for _ in range(3)]
     lib().orc_evaluate(n, _p(m), _p(x), _p(v), _p(a), float(eps), act.size,
                        act.ctypes.data_as(_i32), *[_p(q) for q in out])
+    return tuple(out)
+
+
+def evaluate_kappa(m, x, v, a, eps, active=None):
+    """(sum_j |A_ij|, sum_j |J_ij|, sum_j |S_ij|), each [n_act], for the active list."""
+    m = _f(m)
+    n = m.size
+    x, v, a = _f(x, (n, 3)), _f(v, (n, 3)), _f(a, (n, 3))
+    act = np.arange(n, dtype=np.int32) if active is None else np.ascontiguousarray(
+        active, dtype=np.int32)
+    out = [np.zeros(act.size) for _ in range(3)]
+    lib().orc_evaluate_kappa(n, _p(m), _p(x), _p(v), _p(a), float(eps), act.size,
+                             act.ctypes.data_as(_i32), *[_p(q) for q in out])
     return tuple(out)
 
 

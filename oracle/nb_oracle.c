@@ -104,6 +104,30 @@ void orc_evaluate(int64_t n, const double *m, const double *x, const double *v,
     }
 }
 
+void orc_evaluate_kappa(int64_t n, const double *m, const double *x,
+                        const double *v, const double *a, double eps,
+                        int64_t n_act, const int32_t *act, double *ka,
+                        double *kj, double *ks)
+{
+    for (int64_t k = 0; k < n_act; k++) {
+        int64_t i = act[k];
+        nsum sa = {0, 0}, sj = {0, 0}, ss = {0, 0};
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i)
+                continue;
+            double A[3], J[3], S[3];
+            orc_pair(&x[3 * i], &v[3 * i], &a[3 * i], &x[3 * j], &v[3 * j],
+                     &a[3 * j], m[j], eps, A, J, S);
+            nsum_add(&sa, norm3(A));
+            nsum_add(&sj, norm3(J));
+            nsum_add(&ss, norm3(S));
+        }
+        ka[k] = nsum_value(&sa);
+        kj[k] = nsum_value(&sj);
+        ks[k] = nsum_value(&ss);
+    }
+}
+
 /* ---------------------------------------------------------------- predictor */
 
 /* Predictor stage (section 3): Taylor expansion of each particle from its own

@@ -31,6 +31,15 @@ void orc_evaluate(int64_t n, const double *m, const double *x, const double *v,
                   const double *a, double eps, int64_t n_act, const int32_t *act,
                   double *acc, double *jrk, double *snp);
 
+/* Condition numbers of the evaluation sums: for each listed i, the sums over
+ * j != i of |A_ij|, |J_ij| and |S_ij| (Euclidean norms of the pair terms).
+ * A computed sum carries rounding errors of each term, so its error is
+ * bounded relative to these sums, not to the (possibly cancelling) result. */
+void orc_evaluate_kappa(int64_t n, const double *m, const double *x,
+                        const double *v, const double *a, double eps,
+                        int64_t n_act, const int32_t *act, double *ka,
+                        double *kj, double *ks);
+
 /* Predictor (section 3): Taylor series of x, v, a of every particle from its
  * own time t_i to t, through crackle c. */
 void orc_predict(int64_t n, double t, const double *ti, const double *x,

@@ -107,6 +107,32 @@ def test_jerk_and_snap_are_time_derivatives_of_acc():
         assert err.max() < 1e-6, err.max()
 
 
+def test_kappa_bounds_the_sum_and_equals_it_without_cancellation():
+    m, x, v = ni.plummer(64, 13)
+    a = ni.random_state(64, 14)
+    act = np.arange(0, 64, 5, dtype=np.int32)
+    sums = O.evaluate(m, x, v, a, 1e-3, act)
+    kap = O.evaluate_kappa(m, x, v, a, 1e-3, act)
+    for s_, k_ in zip(sums, kap):
+        assert np.all(np.linalg.norm(s_, axis=1) <= k_ * (1 + 1e-14))
+    # two bodies: one term, no cancellation
+    ka, kj, ks = O.evaluate_kappa(m[:2], x[:2], v[:2], a[:2], 1e-3, [0])
+    A, J, S = O.pair(x[0], v[0], a[0], x[1], v[1], a[1], m[1], 1e-3)
+    assert ka[0] == pytest.approx(np.linalg.norm(A), rel=1e-15)
+    assert kj[0] == pytest.approx(np.linalg.norm(J), rel=1e-15)
+    assert ks[0] == pytest.approx(np.linalg.norm(S), rel=1e-15)
+    # a particle at the centre of a symmetric cube of 8 equal masses at rest:
+    # the acceleration cancels exactly while kappa is 8 |A_one|
+    xc = np.array([[0.0, 0.0, 0.0]] + [[sx, sy, sz] for sx in (-1, 1) for sy in (-1, 1)
+                                        for sz in (-1, 1)])
+    mc = np.ones(9)
+    zero = np.zeros((9, 3))
+    acc = O.evaluate(mc, xc, zero, zero, 1e-3, [0])[0]
+    ka = O.evaluate_kappa(mc, xc, zero, zero, 1e-3, [0])[0]
+    assert np.abs(acc).max() < 1e-15
+    assert ka[0] == pytest.approx(8 * math.sqrt(3) / (3 + 1e-6) ** 1.5, rel=1e-12)
+
+
 # ------------------------------------------------------------- polynomials
 
 def _poly_state(coef, t):

@@ -1,0 +1,472 @@
+#!/usr/bin/env python3
+"""Benchmark of the direct N-body hot path on GB300.
+
+Metric: acc+jerk+snap interactions per second at N = 2^20 (one interaction
+= one (i, j) pair evaluated, the i = j term included, so n_act * N per
+evaluation), mixed precision against FP64, mixed error stated.
+
+Workload (seeded, synthetic): Plummer sphere, N = 2^20, Salpeter masses
+(slope 2.35 on [0.1, 100], total mass 1), Henon units, eps = 1e-4, seed 3.
+One step = one shared block step of the whole path with every particle
+active (the paper's shared-step scheme): predict all N, evaluate all N
+against all N in the mixed kernel, correct + new step.  Inputs resident in
+HBM; the L2 is flushed (256 MB write) before every step, inside the timed
+region.  Secondary numbers: the FP64 kernel at active fraction 2^-5, the
+mixed kernel at active fractions 2^-10 and 2^-5 (split-j), and the mixed
+error against the FP64 GPU path.
+
+--impl reference times the FP64 CPU oracle (the reference arm) on the
+host cores for the same workload, one bounded i-sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_BODY = 1 << 20
+EPS = 1e-4
+SEED = 3
+FLOPS_PER_INTERACTION = 78        # FMA = 2, rsqrt = 1 (counted against the pair formula)
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+# plain-ALU peaks from unit counts and the maximum SM clock
+PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
+PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12     # 1.26
+# DRAM traffic of one mixed evaluation launch from an ncu capture of a
+# smaller case, scaled to the full launch; valid only for the kernel source
+# it was measured on (the sha256 prefix of csrc/k_eval.cu).
+TRAFFIC = {"kernel_sha": None, "bytes_per_launch": None, "source": None}
+WORKLOAD = "plummer_salpeter_N1048576_eps1e-4_shared_step_all_active"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=N_BODY, help="particles (default 2^20)")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    p.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
+    p.add_argument("--profile-eval", action="store_true",
+                   help="only launch the evaluation kernel --reps times on --n particles with "
+                        "--n-act active (a small case for ncu captures)")
+    p.add_argument("--n-act", type=int, default=4096)
+    p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--reps", type=int, default=3)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- CPU leg
+
+def _oracle_worker(args):
+    """Oracle evaluation of i-rows [lo, hi) of the sample; returns seconds."""
+    lo, hi, n = args
+    import numpy as np
+
+    import nb_inputs as ni
+    import oracle as O
+    m, x, v = ni.plummer(n, SEED, imf="salpeter")
+    a = np.zeros_like(x)
+    act = ni.active_subset(n, 4096, 31)[lo:hi]
+    t0 = time.perf_counter()
+    O.evaluate(m, x, v, a, EPS, act)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(n, per_core_rows=48, want_seconds=None):
+    """Single-threaded FP64 oracle timed on (a) one core and (b) one
+    independent instance per usable core on disjoint i-rows of a seeded
+    4096-particle sample, each i against all n j."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0))
+    t1 = _oracle_worker((0, per_core_rows, n))
+    one = per_core_rows * n / t1
+    ctx = mp.get_context("spawn")
+    k = min(cores, 4096 // per_core_rows)
+    jobs = [(r * per_core_rows, (r + 1) * per_core_rows, n) for r in range(k)]
+    with ctx.Pool(k) as pool:
+        secs = pool.map(_oracle_worker, jobs)
+    allc = k * per_core_rows * n / max(secs)   # instances run concurrently
+    return {"value": allc, "unit": "interactions/s", "cores": k, "kind": "oracle",
+            "one_core": one,
+            "sample": f"{k} oracle instances x {per_core_rows} i-particles of a seeded 4096-i "
+                      f"subset x all {n} j (FP64, single-threaded C); one-core run: "
+                      f"{per_core_rows} i x {n} j in {t1:.1f} s",
+            "host_cpu": _cpu_model()}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return os.uname().machine
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    n = args.n
+    rows = 16
+    import nb_inputs as ni  # noqa: F401
+    for _ in range(args.warmup):
+        _oracle_worker((0, 2, n))
+    times = []
+    for s in range(args.steps):
+        times.append(_oracle_worker((s * rows % 4096, s * rows % 4096 + rows, n)))
+    value = rows * n * len(times) / sum(times)
+    line = {"impl": "reference", "metric": "acc+jerk+snap interactions/s at N=2^20 (FP64 CPU oracle)",
+            "value": value, "unit": "interactions/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "eps": EPS, "seed": SEED,
+                       "step": f"oracle evaluation of {rows} sampled i x all {n} j"},
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{rows} i-particles of a seeded 4096-i subset x all {n} j per step"},
+            "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------- GPU leg
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = str(dev)
+        try:
+            import torch
+            self.dev = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+        except Exception:
+            pass
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [q.strip() for q in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    mhz.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, p[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        mhz.sort()
+        return {"sm_mhz": mhz[len(mhz) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def _kernel_sha():
+    with open(os.path.join(ROOT, "paper_1901_08532_gb300", "csrc", "k_eval.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    n = args.n
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(n)          # before any GPU work (spawned pool)
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import nb_inputs as ni
+    import paper_1901_08532_gb300 as nb
+
+    stream = torch.cuda.current_stream()
+    m, x, v = ni.plummer(n, SEED, imf="salpeter")
+    mixed = nb.NBody(m, x, v, EPS, precision=nb.NB_MIXED, dt_shared=2.0 ** -10, stream=stream)
+    st = mixed.state()                      # starting a, jerk, snap from the mixed path
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    def one_step(ctx, ev=None):
+        """Shared block step: predict all, evaluate all, correct all."""
+        flush.zero_()
+        t = ctx_t[0] + 2.0 ** -10
+        ctx.predict(t)
+        if ev is not None:
+            ev[0].record(stream)
+        ctx.evaluate(None, out=False)
+        if ev is not None:
+            ev[1].record(stream)
+        ctx.correct(t)
+        ctx_t[0] = t
+
+    ctx_t = [0.0]
+    for _ in range(args.warmup):
+        one_step(mixed)
+    launches0, inter0 = mixed.counters()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            one_step(mixed, evs[k])
+        barrier()
+        elapsed = time.perf_counter() - t0
+    launches1, inter1 = mixed.counters()
+    eval_ms = [a.elapsed_time(b) for a, b in evs]
+    if world > 1:
+        tt = torch.tensor([elapsed], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    interactions = (inter1 - inter0) * world
+    value = interactions / elapsed
+    eval_s = sum(eval_ms) / len(eval_ms) / 1e3
+    achieved = FLOPS_PER_INTERACTION * float(n) * n / eval_s / 1e12
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernel_sha"] == _kernel_sha() else None
+    clocks = clk.summary()
+
+    extra = {}
+    if not args.no_extra:
+        extra = secondary(nb, np, torch, m, x, v, st, stream, n)
+
+    e2e = end_to_end(nb, np, torch, mixed, n, stream, max(1, min(args.steps, 3)))
+    mixed.close()
+
+    line = {
+        "metric": "acc+jerk+snap interactions/s at N=2^20, mixed vs FP64 at rel err <= 1e-6",
+        "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "precision": "mixed: FP32 pair arithmetic; FP64 positions (hi+lo FP32 "
+                                     "pairs), FP64 prediction/correction, compensated accumulation",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "eps": EPS, "seed": SEED, "imf": "salpeter",
+                   "step": "shared block step, all N active: predict + mixed evaluation + correct",
+                   "l2": "flushed before every step (256 MB write inside the timed region)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "flops_per_interaction": FLOPS_PER_INTERACTION},
+        "roofline": {"bound": "alu", "kernel": "eval_mixed_kernel",
+                     "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / PEAK_FP32_TFLOPS, "traffic": traffic,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit counts "
+                                    "and max clock)",
+                     "eval_ms_mean": 1e3 * eval_s},
+        "e2e": e2e,
+        "gpu_launches": int(launches1 - launches0),
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _time_eval(ctx, torch, stream, act, reps, warm=True):
+    if warm:
+        ctx.evaluate(act, out=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.evaluate(act, out=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def secondary(nb, np, torch, m, x, v, st, stream, n):
+    """FP64 kernel throughput, split-j fractions, mixed error vs FP64."""
+    import nb_inputs as ni
+    out = {}
+    state = {k: st[k] for k in ("x", "v", "a", "j", "s", "c", "t", "dt")}
+    fp64 = nb.NBody(m, x, v, EPS, precision=nb.NB_FP64, dt_shared=2.0 ** -10, stream=stream,
+                    start_forces=False)
+    fp64.set_state(state)
+    mixed = nb.NBody(m, x, v, EPS, precision=nb.NB_MIXED, dt_shared=2.0 ** -10, stream=stream,
+                     start_forces=False)
+    mixed.set_state(state)
+    t = 2.0 ** -10
+    fp64.predict(t)
+    mixed.predict(t)
+    fr = {}
+    act_32k = ni.active_subset(n, n // 32, 32)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    a64, j64, s64_ = fp64.evaluate(act_32k)     # one FP64 launch, timed, results kept
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s64 = e0.elapsed_time(e1) / 1e3
+    fr["fp64_2^-5"] = {"n_act": int(act_32k.size), "interactions_per_s": act_32k.size * n / s64,
+                       "tflops": FLOPS_PER_INTERACTION * act_32k.size * n / s64 / 1e12,
+                       "frac_of_fp64_peak": FLOPS_PER_INTERACTION * act_32k.size * n / s64 / 1e12
+                       / PEAK_FP64_TFLOPS, "tiles": fp64.resolve_tiles(act_32k.size)}
+    for frac, k in (("2^-10", 1024), ("2^-5", 32)):
+        act = ni.active_subset(n, n // k, k)
+        at = torch.from_numpy(act).cuda()
+        sm = _time_eval(mixed, torch, stream, at, 5)
+        fr[f"mixed_{frac}"] = {"n_act": int(act.size), "interactions_per_s": act.size * n / sm,
+                               "frac_of_fp32_peak": FLOPS_PER_INTERACTION * act.size * n / sm / 1e12
+                               / PEAK_FP32_TFLOPS, "tiles": mixed.resolve_tiles(act.size)}
+    out["fractions"] = fr
+    # mixed vs FP64 on the same predicted inputs (the 2^-5 active set)
+    am, jm, sm_ = mixed.evaluate(act_32k)
+    errs = {}
+    for name, g, r in (("acc", am, a64), ("jerk", jm, j64), ("snap", sm_, s64_)):
+        e = np.abs(g - r).max(axis=1) / np.linalg.norm(r, axis=1)
+        errs[name] = {"max": float(e.max()), "p99": float(np.percentile(e, 99)),
+                      "median": float(np.median(e)), "frac_above_1e-6": float((e > 1e-6).mean())}
+    out["mixed_vs_fp64_err"] = {"n_act": int(act_32k.size), "metric": "|d|_inf/|ref|_2 per particle",
+                                **errs}
+    mixed_rate = fr["mixed_2^-5"]["interactions_per_s"]
+    out["speedup_mixed_over_fp64"] = mixed_rate / fr["fp64_2^-5"]["interactions_per_s"]
+    fp64.close()
+    mixed.close()
+    return out
+
+
+def end_to_end(nb, np, torch, ctx, n, stream, steps):
+    """Same metric through the public API with pinned host buffers: upload
+    the full state, one shared block step, read back x and v."""
+    def pinned(shape):
+        return torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    st = ctx.state()
+    host = {k: pinned(st[k].shape) for k in ("x", "v", "a", "j", "s", "c", "t", "dt")}
+    for k in host:
+        host[k][...] = st[k]
+    outx, outv = pinned((n, 3)), pinned((n, 3))
+    ptr = lambda a: a.ctypes.data_as(nb._d)  # noqa: E731
+    lib = nb.lib()
+    h2d = sum(a.nbytes for a in host.values())
+    d2h = outx.nbytes + outv.nbytes
+
+    def step():
+        ctx._check(lib.nb_set_state(ctx._ctx, *[ptr(host[k]) for k in ("x", "v", "a", "j", "s", "c",
+                                                                        "t", "dt")]))
+        ctx.step()
+        ctx._check(lib.nb_get_state(ctx._ctx, ptr(outx), ptr(outv), None, None, None, None, None,
+                                    None))
+    step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return {"value": float(n) * n * steps / el, "unit": "interactions/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "api": "nb_set_state (pinned host) -> nb_step -> nb_get_state (pinned host)",
+            "steps": steps}
+
+
+def profile_eval(args):
+    """Evaluation launches only: Plummer/Salpeter N = --n, --n-act seeded
+    active particles, --reps launches (for ncu; prints per-launch times)."""
+    import numpy as np
+    import torch
+
+    import nb_inputs as ni
+    import paper_1901_08532_gb300 as nb
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    m, x, v = ni.plummer(args.n, SEED, imf="salpeter")
+    a = ni.random_state(args.n, 5, scale=2.0)
+    prec = nb.NB_MIXED if args.prec == "mixed" else nb.NB_FP64
+    ctx = nb.NBody(m, x, v, EPS, precision=prec, stream=stream, start_forces=False)
+    ctx.set_state({"a": a})
+    ctx.predict(0.0)
+    act = torch.from_numpy(ni.active_subset(args.n, args.n_act, 7)).cuda()
+    times = []
+    for _ in range(args.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.evaluate(act, out=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    inter = float(args.n) * args.n_act
+    print(json.dumps({"profile_eval": args.prec, "n": args.n, "n_act": args.n_act,
+                      "tiles": ctx.resolve_tiles(args.n_act), "ms": times,
+                      "interactions_per_s": inter / (min(times) / 1e3)}))
+    ctx.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.profile_eval:
+        return profile_eval(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * libnb -- GB300 (sm_103a) direct N-body hot path: the 6th-order Hermite
+ * predictor / evaluation / corrector with power-of-two block time steps.
+ *
+ * The operations follow the paper's statement of the method (Goz et al.,
+ * "Direct N-body code on low-power embedded ARM GPUs", arXiv:1901.08532):
+ *   - section 2: the device is fed coordinates, velocities and masses and
+ *     returns forces; block time steps with a high-order Hermite scheme;
+ *   - section 3, opening paragraph: predictor, evaluation (acceleration,
+ *     jerk, snap) and corrector stages of the 6th-order Hermite integrator;
+ *   - section 3 item 3: time step by the generalised Aarseth criterion,
+ *     energy and angular momentum evaluated on the device;
+ *   - section 3 item 4 (steps i-iv): the evaluation kernel, j-particles
+ *     cached in on-chip memory, partial sums in registers, self term
+ *     excluded;
+ *   - section 3 item 6 and Eq. 1: precision choice and the energy error.
+ *
+ * Conventions for every entry point
+ *   - Return value: NB_OK (0) or a negative nb_status.  A context whose call
+ *     returned NB_ECUDA must only be passed to nb_last_error and nb_free.
+ *   - Host arrays passed in are read (or written) during the call only; the
+ *     caller keeps ownership.  Vectors are [n][3] row-major doubles.
+ *   - Device pointers passed in are borrowed for the call only and must be
+ *     device memory of the context's device.
+ *   - The context owns all of its device memory (allocated in nb_init,
+ *     released in nb_free) and runs all work on the stream given in
+ *     nb_config.stream (a cudaStream_t; NULL = the legacy default stream).
+ *     Entry points that return host data synchronise that stream.
+ *   - Softened gravity with G = 1: pair term from particle j on particle i
+ *     with r = x_j - x_i, R = |r|^2 + eps^2, A = m_j r / R^(3/2); jerk and
+ *     snap are its first and second time derivatives.  eps > 0 is required,
+ *     which makes the i = j term exactly zero.
+ *   - Times are double; block steps are powers of two, so every time the
+ *     library produces is a dyadic rational computed exactly.
+ */
+#ifndef NB_H
+#define NB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NB_VERSION 1
+
+typedef struct nb_ctx nb_ctx;
+
+typedef enum {
+    NB_OK = 0,
+    NB_EINVAL = -1,     /* bad argument; message in nb_last_error        */
+    NB_ECUDA = -2,      /* CUDA error; the context is no longer usable   */
+    NB_ENOMEM = -3,     /* device or host allocation failed              */
+    NB_ENONFINITE = -4, /* non-finite input, or a non-finite result       */
+    NB_ETIMEOUT = -5,   /* a bounded device-side wait gave up             */
+    NB_ESTATE = -6      /* call out of order (e.g. correct before eval)   */
+} nb_status;
+
+/* Arithmetic of the evaluation step (section 3 item 6).  Prediction,
+ * correction, time steps and energy are FP64 in both modes. */
+typedef enum {
+    NB_FP64 = 0,  /* every operation of the pair sum in IEEE double          */
+    NB_MIXED = 1  /* FP64 positions and accumulation; pair differences
+                     rounded to FP32 (positions as hi + lo FP32 pairs), FP32
+                     rsqrt and pair arithmetic, FP32 sums within a j-tile
+                     folded into a compensated (TwoSum) accumulator         */
+} nb_precision;
+
+/* Shape of the evaluation launch.  0 in any field means "choose
+ * automatically". */
+typedef struct {
+    int32_t ki;       /* i-particles held in registers per thread: 1, 2 or 4  */
+    int32_t threads;  /* threads per block: 32..512, multiple of 32            */
+    int32_t jtile;    /* j-particles per shared-memory stage: multiple of lanes */
+    int32_t lanes;    /* threads sharing one i (j split inside a warp): 1..32  */
+    int32_t split;    /* blocks sharing one i-tile (j split across blocks)     */
+} nb_tiles;
+
+typedef struct {
+    int32_t precision; /* nb_precision                                        */
+    double eta;        /* Aarseth accuracy parameter (0.4)                    */
+    double eta_s;      /* starting-step parameter (0.01)                      */
+    double dt_min;     /* smallest block step (2^-20), a power of two         */
+    double dt_max;     /* largest block step (2^-3), a power of two           */
+    double dt_shared;  /* 0: block steps; > 0: every particle uses this fixed
+                          power-of-two step (the paper's shared step, sec. 3
+                          item 3)                                             */
+    nb_tiles tiles;    /* evaluation launch shape (0 = automatic)             */
+    int32_t start_forces; /* 1: nb_init computes the starting a, jerk, snap and
+                          steps; 0: they start at zero with dt = dt_max and
+                          the caller supplies them with nb_set_state
+                          (checkpoint resume, benchmarks)                     */
+    void *stream;      /* cudaStream_t for all work; NULL = legacy default    */
+} nb_config;
+
+/* Fill cfg with the defaults listed above (FP64, automatic tiles,
+ * start_forces = 1). */
+void nb_config_default(nb_config *cfg);
+
+/* Create a context on the current CUDA device for n particles with masses
+ * m[n], positions x[n][3] and velocities v[n][3] (host arrays, copied) and
+ * softening eps > 0.  Computes the starting acceleration and jerk (one
+ * evaluation pass with a_j = 0), then the snap (a second pass using those
+ * accelerations), sets crackle to zero, t_i = 0 and the starting steps
+ * (eta_s * min(|a|/|j|, sqrt(|a|/|s|)), rounded down to a power of two and
+ * clamped to [dt_min, dt_max]).
+ * Errors: NB_EINVAL (n < 1, n > 2^31 - 1, eps <= 0, bad config), NB_ENONFINITE
+ * (non-finite m, x or v, or m < 0), NB_ENOMEM, NB_ECUDA.  *out is NULL on error. */
+nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
+                  const double *v, double eps, const nb_config *cfg);
+
+/* Predictor (section 3): Taylor-expand x, v and a of EVERY particle from its
+ * own time t_i to t through crackle, into the evaluation buffer.  Does not
+ * change the integrator state.  Errors: NB_EINVAL (non-finite t). */
+nb_status nb_predict(nb_ctx *ctx, double t);
+
+/* Read back the evaluation buffer written by the last nb_predict: predicted
+ * positions, velocities and accelerations ([n][3] host arrays; NULL skips).
+ * NB_FP64 contexts return the FP64 values; NB_MIXED contexts return the
+ * FP32 values the mixed kernel uses (position = hi + lo, evaluated in FP64).
+ * Errors: NB_ESTATE (no prediction yet). */
+nb_status nb_get_predicted(nb_ctx *ctx, double *xp, double *vp, double *ap);
+
+/* Evaluation (section 3 item 4): acceleration, jerk and snap of the n_act
+ * particles listed in active[] (int32 indices in [0, n); NULL means all n in
+ * order, then n_act must equal n) against all n predicted particles from
+ * the last nb_predict, self term excluded.  active is a host pointer, or a
+ * device pointer when active_on_device != 0.  acc, jerk and snap receive
+ * [n_act][3] doubles; they are host pointers, or device pointers when
+ * out_on_device != 0; any of them may be NULL (results are then only kept
+ * for nb_correct).  Indices are checked on the host when active is a host
+ * pointer; device lists are trusted.
+ * Errors: NB_EINVAL (n_act < 0 or > n, bad index), NB_ESTATE (no prediction yet). */
+nb_status nb_evaluate(nb_ctx *ctx, const int32_t *active, int64_t n_act,
+                      int active_on_device, double *acc, double *jerk,
+                      double *snap, int out_on_device);
+
+/* Corrector (section 3) for the particles of the last nb_evaluate, whose
+ * prediction time must equal t: corrected x and v, the new a/jerk/snap,
+ * crackle from quintic interpolation, t_i = t and a new step (generalised
+ * Aarseth criterion, section 3 item 3; shared step when dt_shared > 0).
+ * Errors: NB_ESTATE (no matching evaluation), NB_ENONFINITE (a corrected
+ * value is not finite). */
+nb_status nb_correct(nb_ctx *ctx, double t);
+
+/* One block step, entirely on the device: t_next = min_i(t_i + dt_i), the
+ * active set {i : t_i + dt_i == t_next} (ascending indices), predict all,
+ * evaluate the active set, correct it.  *t_out and *n_act_out (either may
+ * be NULL) receive the step's time and active count. */
+nb_status nb_step(nb_ctx *ctx, double *t_out, int64_t *n_act_out);
+
+/* Block steps until every particle has reached t_end (a multiple of dt_max,
+ * so that all particles synchronise there).  *steps_out may be NULL.
+ * When log_cap > 0, the first log_cap steps are recorded in log_t[] (time)
+ * and log_n[] (active count). */
+nb_status nb_run_until(nb_ctx *ctx, double t_end, int64_t *steps_out,
+                       int64_t log_cap, double *log_t, int64_t *log_n);
+
+/* Kinetic energy sum 1/2 m v^2 and softened potential
+ * -sum_{i<j} m_i m_j / sqrt(r^2 + eps^2) of the current state (section 3
+ * item 3 and Eq. 1); meaningful when all t_i are equal.  FP64, deterministic. */
+nb_status nb_energy(nb_ctx *ctx, double *ekin, double *epot);
+
+/* Angular momentum L = sum m x cross v (L[3]) and sum m |x cross v| (*labs,
+ * may be NULL) of the current state (section 3 item 3, Eq. 1). */
+nb_status nb_angmom(nb_ctx *ctx, double L[3], double *labs);
+
+/* Copy the integrator state to host arrays ([n][3] for vectors, [n] for t
+ * and dt); any pointer may be NULL to skip that field.  c is the crackle. */
+nb_status nb_get_state(nb_ctx *ctx, double *x, double *v, double *a, double *j,
+                       double *s, double *c, double *t, double *dt);
+
+/* Overwrite the integrator state from host arrays (checkpoint resume);
+ * NULL skips a field.  Errors: NB_ENONFINITE, NB_EINVAL (dt not a power of
+ * two in [dt_min, dt_max], or t_i not a multiple of dt_i). */
+nb_status nb_set_state(nb_ctx *ctx, const double *x, const double *v,
+                       const double *a, const double *j, const double *s,
+                       const double *c, const double *t, const double *dt);
+
+/* Indices of the last evaluated active set: up to cap entries into idx[],
+ * the full count in *n_act. */
+nb_status nb_get_active(nb_ctx *ctx, int32_t *idx, int64_t cap, int64_t *n_act);
+
+/* Replace the evaluation launch shape (zero fields = automatic). */
+nb_status nb_set_tiles(nb_ctx *ctx, const nb_tiles *tiles);
+
+/* The launch shape the library would use for n_act active particles under
+ * the current setting (automatic fields resolved). */
+nb_status nb_resolve_tiles(nb_ctx *ctx, int64_t n_act, nb_tiles *out);
+
+/* Counters since nb_init: kernels launched by this context and pair
+ * interactions evaluated (n_act * n per evaluation, self term included). */
+nb_status nb_counters(nb_ctx *ctx, int64_t *launches, double *interactions);
+
+/* Message for the last error of ctx ("" if none).  ctx may be NULL, then
+ * the message of the last failed nb_init on this thread is returned. */
+const char *nb_last_error(const nb_ctx *ctx);
+
+/* Release the context and all of its device memory.  NULL is allowed. */
+void nb_free(nb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NB_H */

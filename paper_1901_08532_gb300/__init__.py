@@ -1,0 +1,285 @@
+"""GB300 (sm_103a) direct N-body hot path: 6th-order Hermite predictor,
+evaluation (acceleration, jerk, snap) and corrector with block time steps.
+
+This module is a thin ctypes binding over the C-ABI library ``libnb.so``
+(declared in ``include/nb.h``): it only marshals arguments.  Every step of
+the path runs in the library's CUDA kernels; there is no CPU fallback.  If
+the library has not been built, importing the module raises ImportError
+(build it with ``python -m paper_1901_08532_gb300.build`` or
+``__graft_entry__.build()``).
+
+PyTorch is used only for device memory and streams: device tensors are
+passed by ``data_ptr()`` and work is issued on
+``torch.cuda.current_stream()``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libnb.so is not built ({LIB_PATH}); run paper_1901_08532_gb300/build.py")
+
+_lib = C.CDLL(LIB_PATH)
+
+NB_OK, NB_EINVAL, NB_ECUDA, NB_ENOMEM, NB_ENONFINITE, NB_ETIMEOUT, NB_ESTATE = 0, -1, -2, -3, -4, -5, -6
+NB_FP64, NB_MIXED = 0, 1
+_STATUS = {NB_EINVAL: "NB_EINVAL", NB_ECUDA: "NB_ECUDA", NB_ENOMEM: "NB_ENOMEM",
+           NB_ENONFINITE: "NB_ENONFINITE", NB_ETIMEOUT: "NB_ETIMEOUT", NB_ESTATE: "NB_ESTATE"}
+
+
+class NBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Tiles(C.Structure):
+    _fields_ = [("ki", C.c_int32), ("threads", C.c_int32), ("jtile", C.c_int32),
+                ("lanes", C.c_int32), ("split", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Config(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("eta", C.c_double), ("eta_s", C.c_double),
+                ("dt_min", C.c_double), ("dt_max", C.c_double), ("dt_shared", C.c_double),
+                ("tiles", Tiles), ("start_forces", C.c_int32), ("stream", C.c_void_p)]
+
+
+_d = C.POINTER(C.c_double)
+_i32 = C.POINTER(C.c_int32)
+_i64 = C.POINTER(C.c_int64)
+_vp = C.c_void_p
+
+_lib.nb_config_default.argtypes = [C.POINTER(Config)]
+_lib.nb_config_default.restype = None
+_lib.nb_init.argtypes = [C.POINTER(C.c_void_p), C.c_int64, _d, _d, _d, C.c_double, C.POINTER(Config)]
+_lib.nb_predict.argtypes = [_vp, C.c_double]
+_lib.nb_get_predicted.argtypes = [_vp, _d, _d, _d]
+_lib.nb_evaluate.argtypes = [_vp, _vp, C.c_int64, C.c_int, _vp, _vp, _vp, C.c_int]
+_lib.nb_correct.argtypes = [_vp, C.c_double]
+_lib.nb_step.argtypes = [_vp, _d, _i64]
+_lib.nb_run_until.argtypes = [_vp, C.c_double, _i64, C.c_int64, _d, _i64]
+_lib.nb_energy.argtypes = [_vp, _d, _d]
+_lib.nb_angmom.argtypes = [_vp, _d, _d]
+_lib.nb_get_state.argtypes = [_vp] + [_d] * 8
+_lib.nb_set_state.argtypes = [_vp] + [_d] * 8
+_lib.nb_get_active.argtypes = [_vp, _i32, C.c_int64, _i64]
+_lib.nb_set_tiles.argtypes = [_vp, C.POINTER(Tiles)]
+_lib.nb_resolve_tiles.argtypes = [_vp, C.c_int64, C.POINTER(Tiles)]
+_lib.nb_counters.argtypes = [_vp, _i64, _d]
+_lib.nb_last_error.argtypes = [_vp]
+_lib.nb_last_error.restype = C.c_char_p
+_lib.nb_free.argtypes = [_vp]
+_lib.nb_free.restype = None
+for _f in ("nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_correct", "nb_step", "nb_run_until",
+           "nb_energy", "nb_angmom", "nb_get_state", "nb_set_state", "nb_get_active",
+           "nb_set_tiles", "nb_resolve_tiles", "nb_counters"):
+    getattr(_lib, _f).restype = C.c_int
+
+EXPORTED = ("nb_config_default", "nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_correct", "nb_step",
+            "nb_run_until", "nb_energy", "nb_angmom", "nb_get_state", "nb_set_state",
+            "nb_get_active", "nb_set_tiles", "nb_resolve_tiles", "nb_counters", "nb_last_error",
+            "nb_free")
+
+
+def lib():
+    """The loaded ctypes library (for direct C-ABI calls)."""
+    return _lib
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.reshape(shape) if shape is not None else a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_d)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class NBody:
+    """One N-body system on the current CUDA device (a libnb context).
+
+    m[n], x[n,3], v[n,3] are host arrays (copied); eps > 0.  precision is
+    NB_FP64 or NB_MIXED.  stream: a torch.cuda.Stream or raw cudaStream_t
+    (default: torch's current stream).
+    """
+
+    def __init__(self, m, x, v, eps, precision=NB_FP64, eta=0.4, eta_s=0.01,
+                 dt_min=2.0 ** -20, dt_max=2.0 ** -3, dt_shared=0.0, tiles=None, stream=None,
+                 start_forces=True):
+        m = _f64(m)
+        n = m.size
+        x, v = _f64(x, (n, 3)), _f64(v, (n, 3))
+        cfg = Config()
+        _lib.nb_config_default(C.byref(cfg))
+        cfg.precision, cfg.eta, cfg.eta_s = precision, eta, eta_s
+        cfg.dt_min, cfg.dt_max, cfg.dt_shared = dt_min, dt_max, dt_shared
+        if tiles:
+            for k, val in dict(tiles).items():
+                setattr(cfg.tiles, k, int(val))
+        cfg.start_forces = 1 if start_forces else 0
+        cfg.stream = _stream_handle(stream)
+        self.n = n
+        self.precision = precision
+        self._ctx = C.c_void_p()
+        st = _lib.nb_init(C.byref(self._ctx), n, _ptr(m), _ptr(x), _ptr(v), float(eps), C.byref(cfg))
+        if st != NB_OK:
+            raise NBError(st, _lib.nb_last_error(None).decode())
+
+    def _check(self, st):
+        if st != NB_OK:
+            raise NBError(st, _lib.nb_last_error(self._ctx).decode())
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            _lib.nb_free(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._ctx.value
+
+    # --- the three stages -------------------------------------------------
+    def predict(self, t):
+        self._check(_lib.nb_predict(self._ctx, float(t)))
+
+    def predicted(self):
+        """(x, v, a) [n, 3] of the evaluation buffer from the last predict()."""
+        out = [np.zeros((self.n, 3)) for _ in range(3)]
+        self._check(_lib.nb_get_predicted(self._ctx, *[_ptr(q) for q in out]))
+        return tuple(out)
+
+    def evaluate(self, active=None, out=None):
+        """Acceleration, jerk, snap of the active particles.
+
+        active: None (all), a host int32 array, or a CUDA int32 tensor.
+        out: None -> returns three numpy [n_act, 3] arrays; "device" ->
+        returns three CUDA float64 tensors; False -> keeps results for
+        correct() only and returns None.
+        """
+        if active is None:
+            aptr, n_act, on_dev = None, self.n, 0
+        elif _is_torch(active) and active.is_cuda:
+            assert active.dtype.__str__() == "torch.int32" and active.is_contiguous()
+            aptr, n_act, on_dev = active.data_ptr(), active.numel(), 1
+        else:
+            active = np.ascontiguousarray(active, dtype=np.int32)
+            aptr, n_act, on_dev = active.ctypes.data, active.size, 0
+        if out is False:
+            self._check(_lib.nb_evaluate(self._ctx, aptr, n_act, on_dev, None, None, None, 0))
+            return None
+        if out == "device":
+            import torch
+            res = [torch.empty((n_act, 3), dtype=torch.float64, device="cuda") for _ in range(3)]
+            self._check(_lib.nb_evaluate(self._ctx, aptr, n_act, on_dev,
+                                         *[r.data_ptr() for r in res], 1))
+            return tuple(res)
+        res = [np.empty((n_act, 3)) for _ in range(3)]
+        self._check(_lib.nb_evaluate(self._ctx, aptr, n_act, on_dev,
+                                     *[r.ctypes.data for r in res], 0))
+        return tuple(res)
+
+    def correct(self, t):
+        self._check(_lib.nb_correct(self._ctx, float(t)))
+
+    # --- integration --------------------------------------------------------
+    def step(self):
+        t = C.c_double()
+        na = C.c_int64()
+        self._check(_lib.nb_step(self._ctx, C.byref(t), C.byref(na)))
+        return t.value, int(na.value)
+
+    def run_until(self, t_end, log_cap=0):
+        steps = C.c_int64()
+        lt = np.zeros(max(1, log_cap))
+        ln = np.zeros(max(1, log_cap), dtype=np.int64)
+        self._check(_lib.nb_run_until(self._ctx, float(t_end), C.byref(steps), int(log_cap),
+                                      _ptr(lt), ln.ctypes.data_as(_i64)))
+        k = min(int(steps.value), log_cap)
+        return int(steps.value), (lt[:k], ln[:k])
+
+    # --- diagnostics and state ---------------------------------------------
+    def energy(self):
+        ek, ep = C.c_double(), C.c_double()
+        self._check(_lib.nb_energy(self._ctx, C.byref(ek), C.byref(ep)))
+        return ek.value, ep.value
+
+    def angmom(self):
+        L = np.zeros(3)
+        la = C.c_double()
+        self._check(_lib.nb_angmom(self._ctx, _ptr(L), C.byref(la)))
+        return L, la.value
+
+    def state(self):
+        n = self.n
+        out = {k: np.zeros((n, 3)) for k in ("x", "v", "a", "j", "s", "c")}
+        out["t"] = np.zeros(n)
+        out["dt"] = np.zeros(n)
+        self._check(_lib.nb_get_state(self._ctx, *[_ptr(out[k]) for k in
+                                                   ("x", "v", "a", "j", "s", "c", "t", "dt")]))
+        return out
+
+    def set_state(self, st):
+        n = self.n
+        args = []
+        for k in ("x", "v", "a", "j", "s", "c"):
+            args.append(_ptr(_f64(st[k], (n, 3))) if k in st else None)
+        for k in ("t", "dt"):
+            args.append(_ptr(_f64(st[k])) if k in st else None)
+        keep = [a for a in args]  # noqa: F841  (arrays stay alive through the call)
+        self._check(_lib.nb_set_state(self._ctx, *args))
+
+    def active(self):
+        na = C.c_int64()
+        self._check(_lib.nb_get_active(self._ctx, None, 0, C.byref(na)))
+        idx = np.zeros(max(1, na.value), dtype=np.int32)
+        self._check(_lib.nb_get_active(self._ctx, idx.ctypes.data_as(_i32), na.value, C.byref(na)))
+        return idx[:na.value]
+
+    def set_tiles(self, **tiles):
+        t = Tiles()
+        for k, val in tiles.items():
+            setattr(t, k, int(val))
+        self._check(_lib.nb_set_tiles(self._ctx, C.byref(t)))
+
+    def resolve_tiles(self, n_act):
+        t = Tiles()
+        self._check(_lib.nb_resolve_tiles(self._ctx, int(n_act), C.byref(t)))
+        return t.as_dict()
+
+    def counters(self):
+        la = C.c_int64()
+        it = C.c_double()
+        self._check(_lib.nb_counters(self._ctx, C.byref(la), C.byref(it)))
+        return int(la.value), float(it.value)

@@ -1,0 +1,260 @@
+// Corrector stage and time-step selection (paper, section 3 and section 3
+// item 3), one thread per active particle, FP64:
+//   * 6th-order Hermite corrector (the two-point quadrature with a, a', a''
+//     at both ends, exact for a(t) of degree <= 5), v first, then x;
+//   * crackle, pop and the 5th derivative of a at the end of the step from
+//     the quintic through (a, jerk, snap) at both ends, in closed form;
+//   * new block step from the generalised Aarseth criterion
+//     eta (A1 / A4)^(1/3), A_k = sqrt(|a^(k-1)| |a^(k+1)|) + |a^(k)|,
+//     rounded down to a power of two, clamped to [dt_min, dt_max], at most
+//     doubled, and doubled only where t1 is a multiple of the doubled step.
+#include "nb_internal.cuh"
+
+namespace {
+
+// Largest power of two <= x for positive normal x (clears the mantissa).
+__device__ __forceinline__ double pow2_floor(double x)
+{
+    return __hiloint2double(__double2hiint(x) & 0x7ff00000, 0);
+}
+
+__device__ double quantise(double crit, double dt_old, double t1, double dt_min, double dt_max,
+                           bool *floor_hit)
+{
+    double p;
+    *floor_hit = false;
+    if (!(crit >= dt_min)) {
+        *floor_hit = true;
+        p = dt_min;
+    } else {
+        p = isinf(crit) ? dt_max : fmin(pow2_floor(crit), dt_max);
+    }
+    if (dt_old > 0.0 && p > dt_old) {
+        const double d2 = 2.0 * dt_old;
+        const double q = t1 * (1.0 / d2);  // exact: d2 is a power of two
+        p = (q == trunc(q)) ? d2 : dt_old;
+    }
+    return p;
+}
+
+struct CorrectArgs {
+    double *st;
+    double *t;
+    double *dt;
+    const int32_t *act;
+    const double *anew;  // [9][ostride]
+    int ostride;
+    int n_act;
+    int n;
+    double t1, eta, dt_min, dt_max, dt_shared;
+    nb_ctl *ctl;
+};
+
+__global__ void __launch_bounds__(128) correct_kernel(CorrectArgs a)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.n_act)
+        return;
+    const size_t N = static_cast<size_t>(a.n);
+    const int i = a.act[k];
+    const double h = a.t1 - a.t[i];
+    const double ih = 1.0 / h;  // exact: h is a sum of powers of two equal to dt_i
+    double n2[6] = {0, 0, 0, 0, 0, 0};  // squared norms of a1, j1, s1, c1, d1, e1
+    bool finite = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double *px = a.st + (F_X * 3 + d) * N + i;
+        double *pv = a.st + (F_V * 3 + d) * N + i;
+        double *pa = a.st + (F_A * 3 + d) * N + i;
+        double *pj = a.st + (F_J * 3 + d) * N + i;
+        double *ps = a.st + (F_S * 3 + d) * N + i;
+        double *pc = a.st + (F_C * 3 + d) * N + i;
+        const double x0 = *px, v0 = *pv, a0 = *pa, j0 = *pj, s0 = *ps;
+        const double a1 = a.anew[(0 + d) * (size_t)a.ostride + k];
+        const double j1 = a.anew[(3 + d) * (size_t)a.ostride + k];
+        const double s1 = a.anew[(6 + d) * (size_t)a.ostride + k];
+        const double v1 =
+            fma(h, fma(h, fma(h, (s0 + s1) * (1.0 / 120.0), -(j1 - j0) * 0.1), 0.5 * (a0 + a1)), v0);
+        const double x1 =
+            fma(h, fma(h, fma(h, (j0 + j1) * (1.0 / 120.0), -(a1 - a0) * 0.1), 0.5 * (v0 + v1)), x0);
+        // quintic through (a, j, s) at both ends: residuals of the cubic
+        // Taylor part, then the inverse of the 3x3 Hermite system
+        const double R1 = a1 - fma(h, fma(0.5 * h, s0, j0), a0);
+        const double R2 = h * (j1 - fma(h, s0, j0));
+        const double R3 = h * h * (s1 - s0);
+        const double ih3 = ih * ih * ih;
+        const double c1 = (60.0 * R1 - 36.0 * R2 + 9.0 * R3) * ih3;
+        const double d1 = (360.0 * R1 - 192.0 * R2 + 36.0 * R3) * ih3 * ih;
+        const double e1 = (720.0 * R1 - 360.0 * R2 + 60.0 * R3) * ih3 * ih * ih;
+        finite = finite && isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1) &&
+                 isfinite(s1) && isfinite(c1);
+        *px = x1;
+        *pv = v1;
+        *pa = a1;
+        *pj = j1;
+        *ps = s1;
+        *pc = c1;
+        n2[0] = fma(a1, a1, n2[0]);
+        n2[1] = fma(j1, j1, n2[1]);
+        n2[2] = fma(s1, s1, n2[2]);
+        n2[3] = fma(c1, c1, n2[3]);
+        n2[4] = fma(d1, d1, n2[4]);
+        n2[5] = fma(e1, e1, n2[5]);
+    }
+    a.t[i] = a.t1;
+    double dtn;
+    bool hit = false;
+    if (a.dt_shared > 0.0) {
+        dtn = a.dt_shared;
+    } else {
+        const double A1 = sqrt(sqrt(n2[0]) * sqrt(n2[2])) + sqrt(n2[1]);
+        const double A4 = sqrt(sqrt(n2[3]) * sqrt(n2[5])) + sqrt(n2[4]);
+        dtn = quantise(a.eta * cbrt(A1 / A4), a.dt[i], a.t1, a.dt_min, a.dt_max, &hit);
+    }
+    a.dt[i] = dtn;
+    if (hit)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->floor_hits), 1ull);
+    if (!finite)
+        atomicOr(&a.ctl->err, NB_ERR_NONFINITE);
+}
+
+// Start-up (nb_init): pass 0 stores a and jerk of the first evaluation (made
+// with a_j = 0); pass 1 stores the snap of the second evaluation and the
+// starting steps eta_s min(|a|/|j|, sqrt(|a|/|s|)).
+__global__ void init_state_kernel(double *st, double *dt, const double *anew, int n, int pass,
+                                  double eta_s, double dt_min, double dt_max, double dt_shared,
+                                  nb_ctl *ctl)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const size_t N = static_cast<size_t>(n);
+    if (pass == 0) {
+        for (int d = 0; d < 3; ++d) {
+            st[(F_A * 3 + d) * N + i] = anew[(0 + d) * N + i];
+            st[(F_J * 3 + d) * N + i] = anew[(3 + d) * N + i];
+        }
+        return;
+    }
+    double na = 0, nj = 0, ns = 0;
+    bool finite = true;
+    for (int d = 0; d < 3; ++d) {
+        const double a = st[(F_A * 3 + d) * N + i], j = st[(F_J * 3 + d) * N + i];
+        const double s = anew[(6 + d) * N + i];
+        st[(F_S * 3 + d) * N + i] = s;
+        st[(F_C * 3 + d) * N + i] = 0.0;
+        na = fma(a, a, na);
+        nj = fma(j, j, nj);
+        ns = fma(s, s, ns);
+        finite = finite && isfinite(a) && isfinite(j) && isfinite(s);
+    }
+    bool hit = false;
+    double d0;
+    if (dt_shared > 0.0) {
+        d0 = dt_shared;
+    } else {
+        na = sqrt(na);
+        const double c1 = na / sqrt(nj), c2 = sqrt(na / sqrt(ns));
+        d0 = quantise(eta_s * fmin(c1, c2), -1.0, 0.0, dt_min, dt_max, &hit);
+    }
+    dt[i] = d0;
+    if (hit)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->floor_hits), 1ull);
+    if (!finite)
+        atomicOr(&ctl->err, NB_ERR_NONFINITE);
+}
+
+// [3][ostride] component rows of anew starting at q0 -> [n_act][3] rows.
+__global__ void transpose_kernel(const double *anew, int ostride, int n_act, int q0, double *dst)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * n_act)
+        return;
+    const int k = e / 3, d = e - 3 * k;
+    dst[e] = anew[(q0 + d) * (size_t)ostride + k];
+}
+
+// State layout conversions: [n][3] rows (the C-ABI's vector layout) <->
+// three component rows of the structure-of-arrays state.
+__global__ void rows_to_soa_kernel(const double *rows, double *soa, int n)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * n)
+        return;
+    const int i = e / 3, d = e - 3 * i;
+    soa[static_cast<size_t>(d) * n + i] = rows[e];
+}
+
+__global__ void soa_to_rows_kernel(const double *soa, double *rows, int n)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * n)
+        return;
+    const int i = e / 3, d = e - 3 * i;
+    rows[e] = soa[static_cast<size_t>(d) * n + i];
+}
+
+}  // namespace
+
+cudaError_t nb_launch_rows_to_soa(nb_ctx *c, const double *rows, int field)
+{
+    const int n = static_cast<int>(c->n);
+    rows_to_soa_kernel<<<(3 * n + 255) / 256, 256, 0, c->stream>>>(
+        rows, c->st + static_cast<size_t>(field) * 3 * n, n);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t nb_launch_soa_to_rows(nb_ctx *c, int field, double *rows)
+{
+    const int n = static_cast<int>(c->n);
+    soa_to_rows_kernel<<<(3 * n + 255) / 256, 256, 0, c->stream>>>(
+        c->st + static_cast<size_t>(field) * 3 * n, rows, n);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t nb_launch_correct(nb_ctx *c, double t1, int n_act)
+{
+    if (n_act <= 0)
+        return cudaSuccess;
+    CorrectArgs a;
+    a.st = c->st;
+    a.t = c->t;
+    a.dt = c->dt;
+    a.act = c->act;
+    a.anew = c->anew;
+    a.ostride = static_cast<int>(c->n);
+    a.n_act = n_act;
+    a.n = static_cast<int>(c->n);
+    a.t1 = t1;
+    a.eta = c->cfg.eta;
+    a.dt_min = c->cfg.dt_min;
+    a.dt_max = c->cfg.dt_max;
+    a.dt_shared = c->cfg.dt_shared;
+    a.ctl = c->ctl;
+    correct_kernel<<<(n_act + 127) / 128, 128, 0, c->stream>>>(a);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t nb_launch_init_state(nb_ctx *c, int pass)
+{
+    const int n = static_cast<int>(c->n);
+    init_state_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(c->st, c->dt, c->anew, n, pass,
+                                                               c->cfg.eta_s, c->cfg.dt_min,
+                                                               c->cfg.dt_max, c->cfg.dt_shared, c->ctl);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t nb_launch_transpose_out(nb_ctx *c, int n_act, int q0, double *dst)
+{
+    if (n_act <= 0)
+        return cudaSuccess;
+    const int total = 3 * n_act;
+    transpose_kernel<<<(total + 255) / 256, 256, 0, c->stream>>>(c->anew, static_cast<int>(c->n), n_act,
+                                                                 q0, dst);
+    c->launches += 1;
+    return cudaGetLastError();
+}

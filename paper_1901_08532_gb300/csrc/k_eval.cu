@@ -1,0 +1,534 @@
+// Evaluation step of the 6th-order Hermite scheme (paper, section 3 item 4):
+// acceleration, jerk and snap of every listed i-particle from all
+// j-particles, Plummer-softened, G = 1.
+//
+// Layout of one launch (GB300, sm_103a):
+//   * grid.x tiles the active list: a block holds (threads / lanes) * KI
+//     i-particles in registers (section 3 item 4 step ii);
+//   * grid.y splits the j-range into `split` contiguous chunks (split-j);
+//   * j-particles stream through shared memory in tiles of `jtile` records,
+//     loaded by 1-D TMA bulk copies into a two-stage mbarrier pipeline
+//     (section 3 item 4 steps i and iii);
+//   * `lanes` consecutive threads share one i and take every lanes-th j of a
+//     tile; their sums are combined with warp shuffles in a fixed order;
+//   * with split > 1 each block writes FP64 partials, and the last block of
+//     an i-tile to finish adds the `split` partials in index order, so the
+//     result does not depend on block scheduling.
+// The self term needs no test: eps > 0 makes r = v = a = 0 contribute 0.
+#include <algorithm>
+
+#include "nb_internal.cuh"
+
+namespace {
+
+// Largest block for KI i-particles per thread (register budget: 255 per
+// thread at 256 threads, 128 at 512).
+__host__ __device__ constexpr int max_threads_for(int ki) { return ki == 1 ? 512 : (ki == 2 ? 256 : 128); }
+
+struct EvalArgs {
+    const void *jb;      // [NC][n] 16-byte records
+    int n;               // j count (= record stride)
+    const int32_t *act;  // [n_act]
+    int n_act;
+    double *out;         // [9][ostride]
+    int ostride;
+    double *part;        // [split][9][n_act] when split > 1
+    unsigned *cnt;       // [gridDim.x] arrival counters, zero between launches
+    int jtile, lanes, split, jchunk;
+    double eps2;
+    nb_ctl *ctl;
+};
+
+template <int NC>
+__device__ __forceinline__ void issue_tile(unsigned char *smem, uint64_t *bar, const EvalArgs &a,
+                                           int stage, int j0, int len)
+{
+    const uint4 *src = static_cast<const uint4 *>(a.jb);
+    uint4 *dst = reinterpret_cast<uint4 *>(smem) + static_cast<size_t>(stage) * NC * a.jtile;
+    nbk::mbar_expect_tx(&bar[stage], static_cast<uint32_t>(NC * len * 16));
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+        nbk::bulk_g2s(dst + c * a.jtile, src + static_cast<size_t>(c) * a.n + j0,
+                      static_cast<uint32_t>(len * 16), &bar[stage]);
+}
+
+// After a timed-out wait: let the copies still in flight land (bounded)
+// before the block's shared memory is released, then flag the error.
+__device__ void drain_after_timeout(uint64_t *bar, int consumed, int issued, nb_ctl *ctl)
+{
+    for (int t = consumed; t < issued; ++t)
+        nbk::mbar_wait_bounded(&bar[t & 1], (t >> 1) & 1, nbk::kWaitLimitNs);
+    atomicOr(&ctl->err, NB_ERR_TIMEOUT);
+}
+
+// Split-j epilogue shared by both precisions: write this block's sums (or
+// partials) and, when split > 1, fold the partials in the last block.
+template <int KI>
+__device__ __forceinline__ void store_or_fold(const EvalArgs &a, double (&acc)[9][KI],
+                                              const int (&kidx)[KI], int lj, int slots, int ibase)
+{
+    __shared__ int s_last;
+    if (lj == 0) {
+#pragma unroll
+        for (int k = 0; k < KI; ++k) {
+            if (kidx[k] < 0)
+                continue;
+            if (a.split == 1) {
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    a.out[static_cast<size_t>(q) * a.ostride + kidx[k]] = acc[q][k];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    a.part[(static_cast<size_t>(blockIdx.y) * 9 + q) * a.n_act + kidx[k]] = acc[q][k];
+            }
+        }
+    }
+    if (a.split == 1)
+        return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_last = (atomicAdd(&a.cnt[blockIdx.x], 1u) == static_cast<unsigned>(a.split - 1));
+    __syncthreads();
+    if (!s_last)
+        return;
+    __threadfence();
+    const int itile = slots * KI;
+    for (int e = threadIdx.x; e < itile * 9; e += blockDim.x) {
+        const int q = e / itile;
+        const int p = ibase + (e - q * itile);
+        if (p >= a.n_act)
+            continue;
+        double s = 0.0;
+        for (int sp = 0; sp < a.split; ++sp)
+            s += __ldcg(&a.part[(static_cast<size_t>(sp) * 9 + q) * a.n_act + p]);
+        a.out[static_cast<size_t>(q) * a.ostride + p] = s;
+    }
+    if (threadIdx.x == 0)
+        a.cnt[blockIdx.x] = 0u;
+}
+
+// ------------------------------------------------------------------ FP64
+
+// One softened pair term in FP64, accumulated into p[0..8]
+// (acc, jerk, snap).  With r, v, a the differences j - i, R = r.r + eps^2,
+// q = R^(-1/2), mu = m_j q^3, alpha = (r.v) q^2, beta = (v.v + r.a) q^2 +
+// alpha^2, u = v - 3 alpha r and w = a - 6 alpha u - 3 beta r:
+//   acc += mu r,  jerk += mu u,  snap += mu w.
+// (jerk = mu v - 3 alpha A and snap = mu a - 6 alpha J - 3 beta A rewritten
+// so that every step is one fused multiply-add.)
+__device__ __forceinline__ void pair_fp64(const double2 &p0, const double2 &p1, const double2 &p2,
+                                          const double2 &p3, const double2 &p4, double xi,
+                                          double yi, double zi, double vxi, double vyi, double vzi,
+                                          double axi, double ayi, double azi, double eps2,
+                                          double *p)
+{
+    const double dx = p0.x - xi, dy = p0.y - yi, dz = p1.x - zi;
+    const double mj = p1.y;
+    const double dvx = p2.x - vxi, dvy = p2.y - vyi, dvz = p3.x - vzi;
+    const double dax = p3.y - axi, day = p4.x - ayi, daz = p4.y - azi;
+    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+    const double rv = fma(dx, dvx, fma(dy, dvy, dz * dvz));
+    const double sv = fma(dx, dax, fma(dy, day, fma(dz, daz, fma(dvx, dvx, fma(dvy, dvy, dvz * dvz)))));
+    const double q = nbk::rsqrt_fp64(r2);
+    const double q2 = q * q;
+    const double mu = mj * q * q2;
+    const double al = rv * q2;
+    const double be = fma(al, al, sv * q2);
+    const double a3 = 3.0 * al, a6 = 6.0 * al, b3 = 3.0 * be;
+    const double ux = fma(-a3, dx, dvx), uy = fma(-a3, dy, dvy), uz = fma(-a3, dz, dvz);
+    const double wx = fma(-a6, ux, fma(-b3, dx, dax));
+    const double wy = fma(-a6, uy, fma(-b3, dy, day));
+    const double wz = fma(-a6, uz, fma(-b3, dz, daz));
+    p[0] = fma(mu, dx, p[0]);
+    p[1] = fma(mu, dy, p[1]);
+    p[2] = fma(mu, dz, p[2]);
+    p[3] = fma(mu, ux, p[3]);
+    p[4] = fma(mu, uy, p[4]);
+    p[5] = fma(mu, uz, p[5]);
+    p[6] = fma(mu, wx, p[6]);
+    p[7] = fma(mu, wy, p[7]);
+    p[8] = fma(mu, wz, p[8]);
+}
+
+template <int KI>
+__global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    constexpr int NC = 5;
+    const int tid = threadIdx.x, lanes = a.lanes, jt = a.jtile;
+    const int slot = tid / lanes, lj = tid - slot * lanes;
+    const int slots = blockDim.x / lanes;
+    const int ibase = blockIdx.x * slots * KI;
+    const double2 *jb = static_cast<const double2 *>(a.jb);
+
+    int kidx[KI];
+    double xi[KI], yi[KI], zi[KI], vxi[KI], vyi[KI], vzi[KI], axi[KI], ayi[KI], azi[KI];
+    double acc[9][KI], part[9][KI];
+#pragma unroll
+    for (int k = 0; k < KI; ++k) {
+        const int p = ibase + slot + k * slots;
+        kidx[k] = p < a.n_act ? p : -1;
+        const int i = a.act[p < a.n_act ? p : a.n_act - 1];
+        const double2 r0 = jb[i], r1 = jb[a.n + i], r2 = jb[2 * (size_t)a.n + i];
+        const double2 r3 = jb[3 * (size_t)a.n + i], r4 = jb[4 * (size_t)a.n + i];
+        xi[k] = r0.x; yi[k] = r0.y; zi[k] = r1.x;
+        vxi[k] = r2.x; vyi[k] = r2.y; vzi[k] = r3.x;
+        axi[k] = r3.y; ayi[k] = r4.x; azi[k] = r4.y;
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            acc[q][k] = 0.0;
+    }
+
+    const int jbeg = blockIdx.y * a.jchunk;
+    const int jend = min(a.n, jbeg + a.jchunk);
+    const int ntiles = jend > jbeg ? (jend - jbeg + jt - 1) / jt : 0;
+    int issued = 0;
+    if (tid == 0) {
+        nbk::mbar_init(&bar[0], 1);
+        nbk::mbar_init(&bar[1], 1);
+        nbk::fence_mbar_init();
+        for (; issued < min(2, ntiles); ++issued)
+            issue_tile<NC>(smem, bar, a, issued, jbeg + issued * jt, min(jt, jend - (jbeg + issued * jt)));
+    }
+    __syncthreads();
+
+    for (int tl = 0; tl < ntiles; ++tl) {
+        const int st = tl & 1;
+        const bool ok = nbk::mbar_wait_bounded(&bar[st], (tl >> 1) & 1, nbk::kWaitLimitNs);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0)
+                drain_after_timeout(bar, tl, issued, a.ctl);
+            return;
+        }
+        const int len = min(jt, jend - (jbeg + tl * jt));
+        const double2 *s = reinterpret_cast<const double2 *>(smem) + static_cast<size_t>(st) * NC * jt;
+#pragma unroll
+        for (int k = 0; k < KI; ++k)
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                part[q][k] = 0.0;
+        for (int jj = lj; jj < len; jj += lanes) {
+            const double2 p0 = s[jj], p1 = s[jt + jj], p2 = s[2 * jt + jj], p3 = s[3 * jt + jj],
+                          p4 = s[4 * jt + jj];
+#pragma unroll
+            for (int k = 0; k < KI; ++k) {
+                double pk[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    pk[q] = part[q][k];
+                pair_fp64(p0, p1, p2, p3, p4, xi[k], yi[k], zi[k], vxi[k], vyi[k], vzi[k], axi[k],
+                          ayi[k], azi[k], a.eps2, pk);
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    part[q][k] = pk[q];
+            }
+        }
+        // two-level summation: tile partial, then running total
+#pragma unroll
+        for (int k = 0; k < KI; ++k)
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                acc[q][k] += part[q][k];
+        __syncthreads();
+        if (tid == 0 && tl + 2 < ntiles) {
+            issue_tile<NC>(smem, bar, a, st, jbeg + (tl + 2) * jt, min(jt, jend - (jbeg + (tl + 2) * jt)));
+            ++issued;
+        }
+    }
+
+    for (int off = lanes >> 1; off > 0; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < KI; ++k)
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                acc[q][k] += __shfl_xor_sync(0xffffffffu, acc[q][k], off);
+    store_or_fold<KI>(a, acc, kidx, lj, slots, ibase);
+}
+
+// ----------------------------------------------------------------- mixed
+
+// The same pair term with FP32 arithmetic.  Position differences are formed
+// from hi/lo FP32 pairs, (xj_hi - xi_hi) + (xj_lo - xi_lo), which keeps them
+// accurate to FP32 rounding of the difference itself even for close pairs
+// far from the origin; velocity and acceleration differences are formed
+// from FP32 copies.  q is the hardware rsqrt estimate after one Newton
+// step.
+__device__ __forceinline__ void pair_mixed(const float4 &h, const float4 &l, const float4 &vv,
+                                           const float4 &aa, const float (&ip)[12], float eps2,
+                                           float *p)
+{
+    const float dx = __fadd_rn(__fsub_rn(h.x, ip[0]), __fsub_rn(l.x, ip[3]));
+    const float dy = __fadd_rn(__fsub_rn(h.y, ip[1]), __fsub_rn(l.y, ip[4]));
+    const float dz = __fadd_rn(__fsub_rn(h.z, ip[2]), __fsub_rn(l.z, ip[5]));
+    const float mj = h.w;
+    const float dvx = vv.x - ip[6], dvy = vv.y - ip[7], dvz = vv.z - ip[8];
+    const float dax = aa.x - ip[9], day = aa.y - ip[10], daz = aa.z - ip[11];
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
+    const float sv = fmaf(dx, dax, fmaf(dy, day, fmaf(dz, daz, fmaf(dvx, dvx, fmaf(dvy, dvy, dvz * dvz)))));
+    float y;
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(r2));
+    // one Newton step, y (1 + h/2) with h = 1 - r2 y^2: the estimate's
+    // 2^-22 error would otherwise reach mu = m q^3 three times over
+    const float hn = fmaf(-r2, y * y, 1.0f);
+    const float q = fmaf(y * hn, 0.5f, y);
+    const float q2 = q * q;
+    const float mu = mj * q * q2;
+    const float al = rv * q2;
+    const float be = fmaf(al, al, sv * q2);
+    const float a3 = 3.0f * al, a6 = 6.0f * al, b3 = 3.0f * be;
+    const float ux = fmaf(-a3, dx, dvx), uy = fmaf(-a3, dy, dvy), uz = fmaf(-a3, dz, dvz);
+    const float wx = fmaf(-a6, ux, fmaf(-b3, dx, dax));
+    const float wy = fmaf(-a6, uy, fmaf(-b3, dy, day));
+    const float wz = fmaf(-a6, uz, fmaf(-b3, dz, daz));
+    p[0] = fmaf(mu, dx, p[0]);
+    p[1] = fmaf(mu, dy, p[1]);
+    p[2] = fmaf(mu, dz, p[2]);
+    p[3] = fmaf(mu, ux, p[3]);
+    p[4] = fmaf(mu, uy, p[4]);
+    p[5] = fmaf(mu, uz, p[5]);
+    p[6] = fmaf(mu, wx, p[6]);
+    p[7] = fmaf(mu, wy, p[7]);
+    p[8] = fmaf(mu, wz, p[8]);
+}
+
+template <int KI>
+__global__ void __launch_bounds__(max_threads_for(KI)) eval_mixed_kernel(EvalArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    constexpr int NC = 4;
+    const int tid = threadIdx.x, lanes = a.lanes, jt = a.jtile;
+    const int slot = tid / lanes, lj = tid - slot * lanes;
+    const int slots = blockDim.x / lanes;
+    const int ibase = blockIdx.x * slots * KI;
+    const float4 *jb = static_cast<const float4 *>(a.jb);
+    const float eps2 = static_cast<float>(a.eps2);
+
+    int kidx[KI];
+    float ip[KI][12];
+    float hi[9][KI], lo[9][KI], part[9][KI];
+#pragma unroll
+    for (int k = 0; k < KI; ++k) {
+        const int p = ibase + slot + k * slots;
+        kidx[k] = p < a.n_act ? p : -1;
+        const int i = a.act[p < a.n_act ? p : a.n_act - 1];
+        const float4 r0 = jb[i], r1 = jb[a.n + i], r2 = jb[2 * (size_t)a.n + i], r3 = jb[3 * (size_t)a.n + i];
+        ip[k][0] = r0.x; ip[k][1] = r0.y; ip[k][2] = r0.z;
+        ip[k][3] = r1.x; ip[k][4] = r1.y; ip[k][5] = r1.z;
+        ip[k][6] = r2.x; ip[k][7] = r2.y; ip[k][8] = r2.z;
+        ip[k][9] = r3.x; ip[k][10] = r3.y; ip[k][11] = r3.z;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            hi[q][k] = 0.0f;
+            lo[q][k] = 0.0f;
+        }
+    }
+
+    const int jbeg = blockIdx.y * a.jchunk;
+    const int jend = min(a.n, jbeg + a.jchunk);
+    const int ntiles = jend > jbeg ? (jend - jbeg + jt - 1) / jt : 0;
+    int issued = 0;
+    if (tid == 0) {
+        nbk::mbar_init(&bar[0], 1);
+        nbk::mbar_init(&bar[1], 1);
+        nbk::fence_mbar_init();
+        for (; issued < min(2, ntiles); ++issued)
+            issue_tile<NC>(smem, bar, a, issued, jbeg + issued * jt, min(jt, jend - (jbeg + issued * jt)));
+    }
+    __syncthreads();
+
+    for (int tl = 0; tl < ntiles; ++tl) {
+        const int st = tl & 1;
+        const bool ok = nbk::mbar_wait_bounded(&bar[st], (tl >> 1) & 1, nbk::kWaitLimitNs);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0)
+                drain_after_timeout(bar, tl, issued, a.ctl);
+            return;
+        }
+        const int len = min(jt, jend - (jbeg + tl * jt));
+        const float4 *s = reinterpret_cast<const float4 *>(smem) + static_cast<size_t>(st) * NC * jt;
+#pragma unroll
+        for (int k = 0; k < KI; ++k)
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                part[q][k] = 0.0f;
+        for (int jj = lj; jj < len; jj += lanes) {
+            const float4 h = s[jj], l = s[jt + jj], vv = s[2 * jt + jj], aa = s[3 * jt + jj];
+#pragma unroll
+            for (int k = 0; k < KI; ++k) {
+                float pk[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    pk[q] = part[q][k];
+                pair_mixed(h, l, vv, aa, ip[k], eps2, pk);
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    part[q][k] = pk[q];
+            }
+        }
+        // fold the FP32 tile sums into the compensated accumulators
+#pragma unroll
+        for (int k = 0; k < KI; ++k)
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                nbk::two_sum_acc(hi[q][k], lo[q][k], part[q][k]);
+        __syncthreads();
+        if (tid == 0 && tl + 2 < ntiles) {
+            issue_tile<NC>(smem, bar, a, st, jbeg + (tl + 2) * jt, min(jt, jend - (jbeg + (tl + 2) * jt)));
+            ++issued;
+        }
+    }
+
+    double acc[9][KI];
+#pragma unroll
+    for (int k = 0; k < KI; ++k)
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            acc[q][k] = static_cast<double>(hi[q][k]) + static_cast<double>(lo[q][k]);
+    for (int off = lanes >> 1; off > 0; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < KI; ++k)
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                acc[q][k] += __shfl_xor_sync(0xffffffffu, acc[q][k], off);
+    store_or_fold<KI>(a, acc, kidx, lj, slots, ibase);
+}
+
+constexpr int kRecBytes64 = 5 * 16;
+constexpr int kRecBytes32 = 4 * 16;
+
+template <typename K>
+cudaError_t set_smem_attr(K kernel)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+}  // namespace
+
+cudaError_t nb_eval_smem_setup()
+{
+    cudaError_t e;
+    if ((e = set_smem_attr(eval_fp64_kernel<1>)) != cudaSuccess) return e;
+    if ((e = set_smem_attr(eval_fp64_kernel<2>)) != cudaSuccess) return e;
+    if ((e = set_smem_attr(eval_fp64_kernel<4>)) != cudaSuccess) return e;
+    if ((e = set_smem_attr(eval_mixed_kernel<1>)) != cudaSuccess) return e;
+    if ((e = set_smem_attr(eval_mixed_kernel<2>)) != cudaSuccess) return e;
+    return set_smem_attr(eval_mixed_kernel<4>);
+}
+
+// Automatic launch shape.  Large active sets: one i per thread slot, no
+// split.  Small ones: lanes share an i so that a block's i-slots are not
+// mostly empty, and the j-range is split across blocks until the grid
+// covers every SM several times.
+nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req)
+{
+    nb_tiles t = req;
+    const bool mixed = c->cfg.precision == NB_MIXED;
+    if (t.threads <= 0)
+        t.threads = 128;
+    if (t.ki <= 0)
+        t.ki = mixed ? 2 : 1;
+    if (t.lanes <= 0) {
+        int l = 1;
+        while (l < 32 && static_cast<int64_t>(t.threads / (2 * l)) * t.ki >= n_act)
+            l *= 2;
+        t.lanes = l;
+    }
+    if (t.jtile <= 0)
+        t.jtile = mixed ? 256 : 128;
+    if (t.jtile % t.lanes)
+        t.jtile = (t.jtile / t.lanes + 1) * t.lanes;
+    if (t.split <= 0) {
+        const int64_t itile = static_cast<int64_t>(t.threads / t.lanes) * t.ki;
+        const int64_t nblk = (n_act + itile - 1) / itile;
+        const int64_t target = static_cast<int64_t>(c->sm_count) * 4;
+        int64_t s = nblk >= target ? 1 : (target + nblk - 1) / nblk;
+        const int64_t max_s = std::max<int64_t>(1, c->n / (2 * t.jtile));
+        s = std::min<int64_t>(std::min<int64_t>(s, max_s), 1024);
+        t.split = static_cast<int32_t>(std::max<int64_t>(1, s));
+    }
+    return t;
+}
+
+cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L)
+{
+    const nb_tiles &t = L.tiles;
+    if (L.n_act <= 0)
+        return cudaSuccess;
+    if (!(t.ki == 1 || t.ki == 2 || t.ki == 4) || t.threads < 32 || t.threads > max_threads_for(t.ki) ||
+        t.threads % 32 || !is_pow2(t.lanes) || t.lanes > 32 || t.jtile < t.lanes ||
+        t.jtile % t.lanes || t.split < 1)
+        return cudaErrorInvalidValue;
+    const bool mixed = c->cfg.precision == NB_MIXED;
+    const int rec = mixed ? kRecBytes32 : kRecBytes64;
+    const size_t smem = static_cast<size_t>(2) * rec * t.jtile;
+    if (smem > 200 * 1024)
+        return cudaErrorInvalidValue;
+    const int itile = (t.threads / t.lanes) * t.ki;
+    const int gx = (L.n_act + itile - 1) / itile;
+    // j chunk per split, a whole number of tiles
+    int64_t chunk = (c->n + t.split - 1) / t.split;
+    chunk = (chunk + t.jtile - 1) / t.jtile * t.jtile;
+    const int split = static_cast<int>((c->n + chunk - 1) / chunk);
+
+    EvalArgs a;
+    a.jb = mixed ? static_cast<const void *>(c->jb32) : static_cast<const void *>(c->jb64);
+    a.n = static_cast<int>(c->n);
+    a.act = L.act;
+    a.n_act = L.n_act;
+    a.out = L.out;
+    a.ostride = L.ostride;
+    a.jtile = t.jtile;
+    a.lanes = t.lanes;
+    a.split = split;
+    a.jchunk = static_cast<int>(chunk);
+    a.eps2 = c->eps * c->eps;
+    a.ctl = c->ctl;
+    a.part = nullptr;
+    a.cnt = nullptr;
+    if (split > 1) {
+        const size_t need = static_cast<size_t>(split) * 9 * L.n_act;
+        if (need > c->part_cap) {
+            cudaFree(c->part);
+            c->part = nullptr;
+            c->part_cap = 0;
+            cudaError_t e = cudaMalloc(&c->part, need * sizeof(double));
+            if (e != cudaSuccess)
+                return e;
+            c->part_cap = need;
+        }
+        if (static_cast<size_t>(gx) > c->tile_cnt_cap) {
+            cudaFree(c->tile_cnt);
+            c->tile_cnt = nullptr;
+            c->tile_cnt_cap = 0;
+            cudaError_t e = cudaMalloc(&c->tile_cnt, static_cast<size_t>(gx) * sizeof(unsigned));
+            if (e != cudaSuccess)
+                return e;
+            e = cudaMemsetAsync(c->tile_cnt, 0, static_cast<size_t>(gx) * sizeof(unsigned), c->stream);
+            if (e != cudaSuccess)
+                return e;
+            c->tile_cnt_cap = gx;
+        }
+        a.part = c->part;
+        a.cnt = c->tile_cnt;
+    }
+    const dim3 grid(gx, split), block(t.threads);
+    if (mixed) {
+        if (t.ki == 1) eval_mixed_kernel<1><<<grid, block, smem, c->stream>>>(a);
+        else if (t.ki == 2) eval_mixed_kernel<2><<<grid, block, smem, c->stream>>>(a);
+        else eval_mixed_kernel<4><<<grid, block, smem, c->stream>>>(a);
+    } else {
+        if (t.ki == 1) eval_fp64_kernel<1><<<grid, block, smem, c->stream>>>(a);
+        else if (t.ki == 2) eval_fp64_kernel<2><<<grid, block, smem, c->stream>>>(a);
+        else eval_fp64_kernel<4><<<grid, block, smem, c->stream>>>(a);
+    }
+    c->launches += 1;
+    c->interactions += static_cast<double>(L.n_act) * static_cast<double>(c->n);
+    return cudaGetLastError();
+}

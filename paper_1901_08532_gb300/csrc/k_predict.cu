@@ -1,0 +1,78 @@
+// Predictor stage of the 6th-order Hermite scheme (paper, section 3): every
+// particle's x, v and a are Taylor-expanded from its own time t_i to the
+// common time t through crackle, in FP64, and written into the record layout
+// the evaluation kernel streams (one coalesced pass; HBM-bound).
+#include "nb_internal.cuh"
+
+namespace {
+
+struct Taylor {
+    double x, v, a;
+};
+
+// Horner form of x + v d + a d^2/2 + j d^3/6 + s d^4/24 + c d^5/120 and its
+// first two derivatives.
+__device__ __forceinline__ Taylor taylor(double x, double v, double a, double j, double s, double c,
+                                         double d)
+{
+    const double d2 = 0.5 * d, d3 = d * (1.0 / 3.0), d4 = 0.25 * d, d5 = 0.2 * d;
+    Taylor r;
+    r.x = fma(d, fma(d2, fma(d3, fma(d4, fma(d5, c, s), j), a), v), x);
+    r.v = fma(d, fma(d2, fma(d3, fma(d4, c, s), j), a), v);
+    r.a = fma(d, fma(d2, fma(d3, c, s), j), a);
+    return r;
+}
+
+__global__ void __launch_bounds__(256) predict_kernel(const double *__restrict__ st,
+                                                      const double *__restrict__ ti,
+                                                      const double *__restrict__ m, int n, double t,
+                                                      double2 *__restrict__ jb64,
+                                                      float4 *__restrict__ jb32)
+{
+    const size_t N = static_cast<size_t>(n);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double d = t - ti[i];
+        Taylor p[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            p[k] = taylor(st[(F_X * 3 + k) * N + i], st[(F_V * 3 + k) * N + i],
+                          st[(F_A * 3 + k) * N + i], st[(F_J * 3 + k) * N + i],
+                          st[(F_S * 3 + k) * N + i], st[(F_C * 3 + k) * N + i], d);
+        const double mi = m[i];
+        if (jb64) {
+            jb64[i] = make_double2(p[0].x, p[1].x);
+            jb64[N + i] = make_double2(p[2].x, mi);
+            jb64[2 * N + i] = make_double2(p[0].v, p[1].v);
+            jb64[3 * N + i] = make_double2(p[2].v, p[0].a);
+            jb64[4 * N + i] = make_double2(p[1].a, p[2].a);
+        }
+        if (jb32) {
+            float hx = __double2float_rn(p[0].x), hy = __double2float_rn(p[1].x),
+                  hz = __double2float_rn(p[2].x);
+            float lx = __double2float_rn(p[0].x - static_cast<double>(hx));
+            float ly = __double2float_rn(p[1].x - static_cast<double>(hy));
+            float lz = __double2float_rn(p[2].x - static_cast<double>(hz));
+            jb32[i] = make_float4(hx, hy, hz, __double2float_rn(mi));
+            jb32[N + i] = make_float4(lx, ly, lz, 0.0f);
+            jb32[2 * N + i] = make_float4(__double2float_rn(p[0].v), __double2float_rn(p[1].v),
+                                          __double2float_rn(p[2].v), 0.0f);
+            jb32[3 * N + i] = make_float4(__double2float_rn(p[0].a), __double2float_rn(p[1].a),
+                                          __double2float_rn(p[2].a), 0.0f);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t nb_launch_predict(nb_ctx *c, double t)
+{
+    const int n = static_cast<int>(c->n);
+    const int block = 256;
+    int grid = (n + block - 1) / block;
+    grid = grid < c->sm_count * 16 ? grid : c->sm_count * 16;
+    const bool mixed = c->cfg.precision == NB_MIXED;
+    predict_kernel<<<grid, block, 0, c->stream>>>(c->st, c->t, c->m, n, t, mixed ? nullptr : c->jb64,
+                                                  mixed ? c->jb32 : nullptr);
+    c->launches += 1;
+    return cudaGetLastError();
+}

@@ -1,0 +1,37 @@
+"""Shared helpers for the parity tests (error metrics, GPU import)."""
+import numpy as np
+import pytest
+
+
+def rel_err(got, ref):
+    """Per-particle error: largest component error over the reference vector
+    norm, |got - ref|_inf / |ref|_2 (rows of [n, 3] arrays)."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    den = np.linalg.norm(ref, axis=1)
+    den = np.where(den > 0, den, 1.0)
+    return np.abs(got - ref).max(axis=1) / den
+
+
+def check_parity(prec, got, ref, kappa=None, tol64=1e-12, tol_mixed=1e-6):
+    """FP64 (prec 0): |got - ref|_inf <= tol64 |ref|_2 per particle.
+    Mixed (prec 1): |got - ref|_inf <= tol_mixed * kappa per particle, with
+    kappa = sum_j |T_ij| the condition number of the sum (the FP32 pair terms
+    each carry rounding errors of a few 1e-8 relative to |T_ij|).  Returns
+    the worst ratio to the bound."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    if prec == 0:
+        return float((rel_err(got, ref) / tol64).max()) if len(ref) else 0.0
+    assert kappa is not None
+    err = np.abs(got - ref).max(axis=1)
+    return float((err / (tol_mixed * np.asarray(kappa))).max()) if len(ref) else 0.0
+
+
+def nb_gpu():
+    """The CUDA package, or skip when no GPU is present."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1901_08532_gb300 as nb
+    return nb

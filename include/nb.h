@@ -192,6 +192,40 @@ nb_status nb_resolve_tiles(nb_ctx *ctx, int64_t n_act, nb_tiles *out);
  * interactions evaluated (n_act * n per evaluation, self term included). */
 nb_status nb_counters(nb_ctx *ctx, int64_t *launches, double *interactions);
 
+/* Allocation-free FP64 evaluation.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory: a host
+ * application that owns all GPU memory through its own pool or caching
+ * allocator and forbids raw cudaMalloc (which would bypass the pool's
+ * accounting); a latency-critical loop where cudaMalloc/cudaFree, which can
+ * synchronise the device, are not acceptable; a deployment whose memory
+ * must all be reserved before it starts.  It evaluates the same sums as
+ * nb_evaluate on an NB_FP64 context and calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *   jrec    device, 5 arrays of n 16-byte records: jrec[c * n + i] holds
+ *           (x, y), (z, m), (vx, vy), (vz, ax), (ay, az) for c = 0..4 (the
+ *           predicted particles; 16-byte aligned)
+ *   active  device, n_act int32 indices in [0, n) (not checked)
+ *   out     device, [9][n_act] doubles: row q * n_act + k holds acc x, y, z,
+ *           jerk x, y, z, snap x, y, z (q = 0..8) of particle active[k]
+ *   split   0: automatic; > 0: that many blocks share each i-tile
+ *   stream  cudaStream_t (NULL: legacy default stream); the call only
+ *           enqueues work and does not synchronise
+ * Scratch: the j-split partial sums and counters use a fixed 16 MiB array
+ * inside the library, reserved on every GPU that loads it until the
+ * library is unloaded.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call clears the counters it
+ * uses and otherwise reuses the array, so calls whose work overlaps on the
+ * GPU (other streams, other threads) race on it and must be serialised.
+ * A device-side wait that times out leaves out incomplete; this entry
+ * point does not report it.
+ * Errors (message via nb_last_error(NULL)): NB_EINVAL (bad argument, or an
+ * explicit split whose partials, split * 9 * n_act doubles, exceed the
+ * scratch), NB_ECUDA. */
+nb_status nb_evaluate_fp64_static(const void *jrec, int64_t n, const int32_t *active,
+                                  int64_t n_act, double eps, int32_t split, double *out,
+                                  void *stream);
+
 /* Message for the last error of ctx ("" if none).  ctx may be NULL, then
  * the message of the last failed nb_init on this thread is returned. */
 const char *nb_last_error(const nb_ctx *ctx);

@@ -76,6 +76,9 @@ _lib.nb_get_active.argtypes = [_vp, _i32, C.c_int64, _i64]
 _lib.nb_set_tiles.argtypes = [_vp, C.POINTER(Tiles)]
 _lib.nb_resolve_tiles.argtypes = [_vp, C.c_int64, C.POINTER(Tiles)]
 _lib.nb_counters.argtypes = [_vp, _i64, _d]
+_lib.nb_evaluate_fp64_static.argtypes = [_vp, C.c_int64, _vp, C.c_int64, C.c_double, C.c_int32,
+                                         _vp, _vp]
+_lib.nb_evaluate_fp64_static.restype = C.c_int
 _lib.nb_last_error.argtypes = [_vp]
 _lib.nb_last_error.restype = C.c_char_p
 _lib.nb_free.argtypes = [_vp]
@@ -87,8 +90,8 @@ for _f in ("nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_corre
 
 EXPORTED = ("nb_config_default", "nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_correct", "nb_step",
             "nb_run_until", "nb_energy", "nb_angmom", "nb_get_state", "nb_set_state",
-            "nb_get_active", "nb_set_tiles", "nb_resolve_tiles", "nb_counters", "nb_last_error",
-            "nb_free")
+            "nb_get_active", "nb_set_tiles", "nb_resolve_tiles", "nb_counters",
+            "nb_evaluate_fp64_static", "nb_last_error", "nb_free")
 
 
 def lib():

@@ -16,6 +16,7 @@
 //     result does not depend on block scheduling.
 // The self term needs no test: eps > 0 makes r = v = a = 0 contribute 0.
 #include <algorithm>
+#include <mutex>
 
 #include "nb_internal.cuh"
 
@@ -531,4 +532,143 @@ cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L)
     c->launches += 1;
     c->interactions += static_cast<double>(L.n_act) * static_cast<double>(c->n);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------ allocation-free variant
+//
+// For callers that must not allocate device memory, the FP64 evaluation can
+// run with its split-j scratch (partial sums and arrival counters) in a
+// fixed array that lives in the library image.  The array is reserved on
+// every GPU that loads the library, for as long as the library stays loaded.
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB per device
+constexpr size_t kStaticCtlBytes = 256;                    // nb_ctl (error flags)
+constexpr int kStaticMaxTiles = 4096;                      // arrival counters
+constexpr size_t kStaticPartOffset = kStaticCtlBytes + sizeof(unsigned) * kStaticMaxTiles;
+constexpr size_t kStaticPartDoubles = (kStaticScratchBytes - kStaticPartOffset) / sizeof(double);
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+void *g_static_addr[kMaxDevices] = {};  // device address of g_static_scratch, per device
+
+// Per-device set-up (with that device current): the array's device address
+// and the kernel's shared-memory limit.  Host code may not use the array's
+// name as an address; it is a host-side stand-in.
+nb_status static_setup(int dev, void **addr)
+{
+    if (dev < 0 || dev >= kMaxDevices) {
+        nb_set_thread_error("nb_evaluate_fp64_static: device ordinal out of range");
+        return NB_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) {
+            nb_set_thread_error(cudaGetErrorString(e));
+            return NB_ECUDA;
+        }
+        e = set_smem_attr(eval_fp64_kernel<1>);
+        if (e != cudaSuccess) {
+            nb_set_thread_error(cudaGetErrorString(e));
+            return NB_ECUDA;
+        }
+        g_static_addr[dev] = p;
+    }
+    *addr = g_static_addr[dev];
+    return NB_OK;
+}
+
+}  // namespace
+
+extern "C" nb_status nb_evaluate_fp64_static(const void *jrec, int64_t n, const int32_t *active,
+                                             int64_t n_act, double eps, int32_t split, double *out,
+                                             void *stream)
+{
+    if (!jrec || !active || !out || n < 1 || n > 0x7fffffffLL || n_act < 0 || n_act > n ||
+        split < 0 || !(eps >= 0x1p-60) || !(eps <= 1e18)) {
+        nb_set_thread_error("nb_evaluate_fp64_static: invalid argument");
+        return NB_EINVAL;
+    }
+    if (n_act == 0)
+        return NB_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        nb_set_thread_error(cudaGetErrorString(e));
+        return NB_ECUDA;
+    }
+    void *base = nullptr;
+    nb_status st = static_setup(dev, &base);
+    if (st != NB_OK)
+        return st;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        nb_set_thread_error(cudaGetErrorString(e));
+        return NB_ECUDA;
+    }
+
+    // launch shape: one i per thread slot, lanes share an i for small sets
+    const int threads = 128, jt = 128;
+    int lanes = 1;
+    while (lanes < 32 && static_cast<int64_t>(threads / (2 * lanes)) >= n_act)
+        lanes *= 2;
+    const int itile = threads / lanes;
+    const int64_t gx = (n_act + itile - 1) / itile;
+    const size_t part_per_split = static_cast<size_t>(9) * n_act;
+    int64_t s = split;
+    if (s == 0) {
+        const int64_t target = static_cast<int64_t>(sms) * 4;
+        s = gx >= target ? 1 : (target + gx - 1) / gx;
+        s = std::min<int64_t>(s, std::max<int64_t>(1, n / (2 * jt)));
+        s = std::min<int64_t>(s, static_cast<int64_t>(kStaticPartDoubles / part_per_split));
+        if (gx > kStaticMaxTiles)
+            s = 1;
+        s = std::max<int64_t>(1, s);
+    } else if (s > 1 && (static_cast<size_t>(s) * part_per_split > kStaticPartDoubles ||
+                         gx > kStaticMaxTiles)) {
+        nb_set_thread_error("nb_evaluate_fp64_static: split * 9 * n_act doubles exceed the "
+                            "16 MiB static scratch");
+        return NB_EINVAL;
+    }
+    int64_t chunk = (n + s - 1) / s;
+    chunk = (chunk + jt - 1) / jt * jt;
+    const int splits = static_cast<int>((n + chunk - 1) / chunk);
+
+    cudaStream_t strm = static_cast<cudaStream_t>(stream);
+    unsigned char *b = static_cast<unsigned char *>(base);
+    // every call clears the error word and the counters it may use
+    e = cudaMemsetAsync(b, 0, kStaticPartOffset, strm);
+    if (e != cudaSuccess) {
+        nb_set_thread_error(cudaGetErrorString(e));
+        return NB_ECUDA;
+    }
+    EvalArgs a;
+    a.jb = jrec;
+    a.n = static_cast<int>(n);
+    a.act = active;
+    a.n_act = static_cast<int>(n_act);
+    a.out = out;
+    a.ostride = static_cast<int>(n_act);
+    a.part = splits > 1 ? reinterpret_cast<double *>(b + kStaticPartOffset) : nullptr;
+    a.cnt = splits > 1 ? reinterpret_cast<unsigned *>(b + kStaticCtlBytes) : nullptr;
+    a.jtile = jt;
+    a.lanes = lanes;
+    a.split = splits;
+    a.jchunk = static_cast<int>(chunk);
+    a.eps2 = eps * eps;
+    a.ctl = reinterpret_cast<nb_ctl *>(b);
+    const size_t smem = static_cast<size_t>(2) * kRecBytes64 * jt;
+    eval_fp64_kernel<1><<<dim3(static_cast<unsigned>(gx), splits), threads, smem, strm>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        nb_set_thread_error(cudaGetErrorString(e));
+        return NB_ECUDA;
+    }
+    return NB_OK;
 }

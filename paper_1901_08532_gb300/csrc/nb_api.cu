@@ -185,6 +185,11 @@ void free_all(nb_ctx *c)
 
 }  // namespace
 
+void nb_set_thread_error(const char *msg)
+{
+    g_init_err = msg ? msg : "";
+}
+
 extern "C" {
 
 void nb_config_default(nb_config *cfg)

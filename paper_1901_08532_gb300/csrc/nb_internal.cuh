@@ -207,6 +207,8 @@ cudaError_t nb_launch_soa_to_rows(nb_ctx *c, int field, double *rows);
 // k_sched.cu
 cudaError_t nb_launch_schedule(nb_ctx *c);
 cudaError_t nb_launch_iota(nb_ctx *c, int n);
+// nb_api.cu: message returned by nb_last_error(NULL) on this thread
+void nb_set_thread_error(const char *msg);
 // k_energy.cu
 cudaError_t nb_launch_energy(nb_ctx *c, double *ek_pe_dev);
 cudaError_t nb_launch_angmom(nb_ctx *c, double *l4_dev);

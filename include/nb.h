@@ -69,11 +69,12 @@ typedef enum {
 /* Shape of the evaluation launch.  0 in any field means "choose
  * automatically". */
 typedef struct {
-    int32_t ki;       /* i-particles held in registers per thread: 1, 2 or 4  */
+    int32_t ki;       /* i-particles per thread: 1, 2 or 4 (mixed: 1 or 2)    */
     int32_t threads;  /* threads per block: 32..512, multiple of 32            */
     int32_t jtile;    /* j-particles per shared-memory stage: multiple of lanes */
     int32_t lanes;    /* threads sharing one i (j split inside a warp): 1..32  */
     int32_t split;    /* blocks sharing one i-tile (j split across blocks)     */
+    int32_t junroll;  /* mixed path: j per inner iteration, 2 or 4            */
 } nb_tiles;
 
 typedef struct {

@@ -42,7 +42,7 @@ class NBError(RuntimeError):
 
 class Tiles(C.Structure):
     _fields_ = [("ki", C.c_int32), ("threads", C.c_int32), ("jtile", C.c_int32),
-                ("lanes", C.c_int32), ("split", C.c_int32)]
+                ("lanes", C.c_int32), ("split", C.c_int32), ("junroll", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

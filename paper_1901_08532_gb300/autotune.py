@@ -1,0 +1,136 @@
+"""Launch-shape autotuner for the evaluation kernels.
+
+For a given system size and active-set size it times candidate launch
+shapes (i-particles per thread, threads per block, j-tile length, j per
+inner iteration; lanes and split-j are resolved by the library for each
+shape) through the C-ABI (nb_set_tiles + nb_evaluate, CUDA events on the
+context's stream) and keeps the fastest.  Results are cached per
+(precision, n, n_act bucket) in memory and, optionally, in a JSON file.
+
+Command line (prints one JSON line per timed shape, then the best):
+    python -m paper_1901_08532_gb300.autotune --n 1048576 --n-act 1024 --prec mixed
+"""
+from __future__ import annotations
+
+import argparse
+import itertools
+import json
+import math
+import os
+
+MIXED_SPACE = {"ki": (1, 2), "junroll": (2, 4), "threads": (64, 128, 256), "jtile": (256, 512)}
+FP64_SPACE = {"ki": (1, 2), "threads": (64, 128, 256), "jtile": (128, 256)}
+
+_cache: dict = {}
+
+
+def _bucket(n_act: int) -> int:
+    return 1 << max(0, math.ceil(math.log2(max(1, n_act))))
+
+
+def candidates(precision: int):
+    space = MIXED_SPACE if precision == 1 else FP64_SPACE
+    keys = sorted(space)
+    for vals in itertools.product(*(space[k] for k in keys)):
+        shape = dict(zip(keys, vals))
+        if precision == 1 and shape["ki"] == 2 and shape["threads"] > 128:
+            continue
+        if shape["ki"] == 2 and shape["threads"] > 256:
+            continue
+        yield shape
+
+
+def time_shape(ctx, shape, active, reps=3):
+    """Mean seconds of one evaluation of `active` (a CUDA int32 tensor) with
+    the given launch shape; None if the library rejects the shape."""
+    import torch
+    import paper_1901_08532_gb300 as nb
+    try:
+        ctx.set_tiles(**shape)
+        ctx.evaluate(active, out=False)
+    except nb.NBError:
+        return None
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.evaluate(active, out=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def tune(ctx, active, reps=3, log=None, cache_file=None):
+    """Pick the fastest shape for evaluating `active` on `ctx` and leave it
+    set on the context.  Returns (shape, seconds)."""
+    key = (ctx.precision, ctx.n, _bucket(int(active.numel())))
+    if key not in _cache and cache_file and os.path.exists(cache_file):
+        with open(cache_file) as f:
+            for k, v in json.load(f).items():
+                _cache[tuple(json.loads(k))] = (v["shape"], v["seconds"])
+    if key in _cache:
+        shape, sec = _cache[key]
+        ctx.set_tiles(**shape)
+        return shape, sec
+    best = (None, float("inf"))
+    for shape in candidates(ctx.precision):
+        sec = time_shape(ctx, shape, active, reps)
+        if log is not None:
+            log({"shape": shape, "resolved": ctx.resolve_tiles(int(active.numel())) if sec else None,
+                 "seconds": sec})
+        if sec is not None and sec < best[1]:
+            best = (shape, sec)
+    if best[0] is None:
+        ctx.set_tiles()
+        return None, None
+    _cache[key] = best
+    ctx.set_tiles(**best[0])
+    if cache_file:
+        data = {}
+        if os.path.exists(cache_file):
+            with open(cache_file) as f:
+                data = json.load(f)
+        data[json.dumps(list(key))] = {"shape": best[0], "seconds": best[1]}
+        with open(cache_file, "w") as f:
+            json.dump(data, f, indent=1)
+    return best
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--n", type=int, default=1 << 20)
+    p.add_argument("--n-act", type=int, nargs="+", default=[1024])
+    p.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--seed", type=int, default=3)
+    args = p.parse_args()
+    import torch
+
+    import nb_inputs as ni
+    import paper_1901_08532_gb300 as nb
+    torch.cuda.set_device(0)
+    m, x, v = ni.plummer(args.n, args.seed, imf="salpeter")
+    prec = nb.NB_MIXED if args.prec == "mixed" else nb.NB_FP64
+    ctx = nb.NBody(m, x, v, 1e-4, precision=prec, start_forces=False)
+    ctx.set_state({"a": ni.random_state(args.n, 5, scale=2.0)})
+    ctx.predict(0.0)
+    for n_act in args.n_act:
+        act = torch.from_numpy(ni.active_subset(args.n, n_act, 7)).cuda()
+
+        def log(rec, n_act=n_act):
+            sec = rec["seconds"]
+            rec.update(n=args.n, n_act=n_act, prec=args.prec,
+                       interactions_per_s=(float(args.n) * n_act / sec) if sec else None)
+            print(json.dumps(rec), flush=True)
+
+        shape, sec = tune(ctx, act, args.reps, log=log)
+        print(json.dumps({"best": shape, "n": args.n, "n_act": n_act, "prec": args.prec,
+                          "seconds": sec,
+                          "interactions_per_s": float(args.n) * n_act / sec if sec else None}),
+              flush=True)
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -250,83 +250,137 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs
 }
 
 // ----------------------------------------------------------------- mixed
+//
+// FP32 pair arithmetic in packed form: every f32x2 instruction works on two
+// j-particles at once (fma.rn.f32x2 and friends, sm_100+), which halves the
+// issue slots the pair formula needs, so the FP32 pipe rather than
+// instruction issue sets the pace.  The j-tile sits in shared memory as 13
+// FP32 rows, so two (or four) consecutive j of one component load as one
+// 64- (128-) bit word; the i-particle's values are held negated and
+// duplicated into both halves of a pair.
+//
+// Position differences are formed from hi/lo FP32 pairs,
+// (xj_hi - xi_hi) + (xj_lo - xi_lo), which keeps them accurate to FP32
+// rounding of the difference itself even for close pairs far from the
+// origin; velocity and acceleration differences use FP32 copies.  q and q^2
+// are separate special-function-unit estimates of R^(-1/2) and 1/R (which
+// moves their cost off the FMA pipe).  Each thread sums a tile in
+// FP32 (two halves), then folds the tile sum into a TwoSum-compensated
+// (hi, lo) accumulator.
 
-// The same pair term with FP32 arithmetic.  Position differences are formed
-// from hi/lo FP32 pairs, (xj_hi - xi_hi) + (xj_lo - xi_lo), which keeps them
-// accurate to FP32 rounding of the difference itself even for close pairs
-// far from the origin; velocity and acceleration differences are formed
-// from FP32 copies.  q is the hardware rsqrt estimate after one Newton
-// step.
-__device__ __forceinline__ void pair_mixed(const float4 &h, const float4 &l, const float4 &vv,
-                                           const float4 &aa, const float (&ip)[12], float eps2,
-                                           float *p)
+constexpr int NCF = 13;  // FP32 rows of the mixed j-buffer
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ float rsqrt_est(float x)
 {
-    const float dx = __fadd_rn(__fsub_rn(h.x, ip[0]), __fsub_rn(l.x, ip[3]));
-    const float dy = __fadd_rn(__fsub_rn(h.y, ip[1]), __fsub_rn(l.y, ip[4]));
-    const float dz = __fadd_rn(__fsub_rn(h.z, ip[2]), __fsub_rn(l.z, ip[5]));
-    const float mj = h.w;
-    const float dvx = vv.x - ip[6], dvy = vv.y - ip[7], dvz = vv.z - ip[8];
-    const float dax = aa.x - ip[9], day = aa.y - ip[10], daz = aa.z - ip[11];
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-    const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
-    const float sv = fmaf(dx, dax, fmaf(dy, day, fmaf(dz, daz, fmaf(dvx, dvx, fmaf(dvy, dvy, dvz * dvz)))));
     float y;
-    asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(r2));
-    // one Newton step, y (1 + h/2) with h = 1 - r2 y^2: the estimate's
-    // 2^-22 error would otherwise reach mu = m q^3 three times over
-    const float hn = fmaf(-r2, y * y, 1.0f);
-    const float q = fmaf(y * hn, 0.5f, y);
-    const float q2 = q * q;
-    const float mu = mj * q * q2;
-    const float al = rv * q2;
-    const float be = fmaf(al, al, sv * q2);
-    const float a3 = 3.0f * al, a6 = 6.0f * al, b3 = 3.0f * be;
-    const float ux = fmaf(-a3, dx, dvx), uy = fmaf(-a3, dy, dvy), uz = fmaf(-a3, dz, dvz);
-    const float wx = fmaf(-a6, ux, fmaf(-b3, dx, dax));
-    const float wy = fmaf(-a6, uy, fmaf(-b3, dy, day));
-    const float wz = fmaf(-a6, uz, fmaf(-b3, dz, daz));
-    p[0] = fmaf(mu, dx, p[0]);
-    p[1] = fmaf(mu, dy, p[1]);
-    p[2] = fmaf(mu, dz, p[2]);
-    p[3] = fmaf(mu, ux, p[3]);
-    p[4] = fmaf(mu, uy, p[4]);
-    p[5] = fmaf(mu, uz, p[5]);
-    p[6] = fmaf(mu, wx, p[6]);
-    p[7] = fmaf(mu, wy, p[7]);
-    p[8] = fmaf(mu, wz, p[8]);
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
-template <int KI>
-__global__ void __launch_bounds__(max_threads_for(KI)) eval_mixed_kernel(EvalArgs a)
+__device__ __forceinline__ float rcp_est(float x)
+{
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Two pair terms (j, j+1) for one i.  c[] are the 13 j-rows (as pairs), ni[]
+// the negated i-values (-xh,-yh,-zh,-xl,-yl,-zl,-vx,-vy,-vz,-ax,-ay,-az).
+// With r, v, a = j - i, R = r.r + eps^2, q = R^(-1/2), mu = m_j q^3,
+// alpha = (r.v) q^2, beta = (v.v + r.a) q^2 + alpha^2, u = v - 3 alpha r and
+// w = a - 6 alpha u - 3 beta r:  acc += mu r, jerk += mu u, snap += mu w.
+__device__ __forceinline__ void pair_mixed2(const float2 (&c)[NCF], const float2 (&ni)[12],
+                                            float2 eps2, float2 (&p)[9])
+{
+    const float2 dx = add2(add2(c[0], ni[0]), add2(c[4], ni[3]));
+    const float2 dy = add2(add2(c[1], ni[1]), add2(c[5], ni[4]));
+    const float2 dz = add2(add2(c[2], ni[2]), add2(c[6], ni[5]));
+    const float2 dvx = add2(c[7], ni[6]), dvy = add2(c[8], ni[7]), dvz = add2(c[9], ni[8]);
+    const float2 dax = add2(c[10], ni[9]), day = add2(c[11], ni[10]), daz = add2(c[12], ni[11]);
+    const float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
+    const float2 rv = fma2(dx, dvx, fma2(dy, dvy, mul2(dz, dvz)));
+    const float2 sv = fma2(dx, dax, fma2(dy, day, fma2(dz, daz, fma2(dvx, dvx, fma2(dvy, dvy, mul2(dvz, dvz))))));
+    // q = R^(-1/2) and q^2 = 1/R both from the special-function unit, so the
+    // squaring error of an estimate does not enter mu = m q^3 and alpha/beta
+    const float2 q = make_float2(rsqrt_est(r2.x), rsqrt_est(r2.y));
+    const float2 q2 = make_float2(rcp_est(r2.x), rcp_est(r2.y));
+    const float2 mu = mul2(mul2(c[3], q), q2);
+    const float2 al = mul2(rv, q2);
+    const float2 be = fma2(al, al, mul2(sv, q2));
+    const float2 na3 = mul2(al, f2(-3.0f)), na6 = mul2(al, f2(-6.0f)), nb3 = mul2(be, f2(-3.0f));
+    const float2 ux = fma2(na3, dx, dvx), uy = fma2(na3, dy, dvy), uz = fma2(na3, dz, dvz);
+    const float2 wx = fma2(na6, ux, fma2(nb3, dx, dax));
+    const float2 wy = fma2(na6, uy, fma2(nb3, dy, day));
+    const float2 wz = fma2(na6, uz, fma2(nb3, dz, daz));
+    p[0] = fma2(mu, dx, p[0]);
+    p[1] = fma2(mu, dy, p[1]);
+    p[2] = fma2(mu, dz, p[2]);
+    p[3] = fma2(mu, ux, p[3]);
+    p[4] = fma2(mu, uy, p[4]);
+    p[5] = fma2(mu, uz, p[5]);
+    p[6] = fma2(mu, wx, p[6]);
+    p[7] = fma2(mu, wy, p[7]);
+    p[8] = fma2(mu, wz, p[8]);
+}
+
+// 13 bulk copies per tile, one per FP32 row; len and j0 are multiples of 4.
+__device__ __forceinline__ void issue_tile_rows(unsigned char *smem, uint64_t *bar, const EvalArgs &a,
+                                                int stage, int j0, int len)
+{
+    const float *src = static_cast<const float *>(a.jb);
+    float *dst = reinterpret_cast<float *>(smem) + static_cast<size_t>(stage) * NCF * a.jtile;
+    nbk::mbar_expect_tx(&bar[stage], static_cast<uint32_t>(NCF * len * 4));
+#pragma unroll
+    for (int c = 0; c < NCF; ++c)
+        nbk::bulk_g2s(dst + c * a.jtile, src + static_cast<size_t>(c) * a.n + j0,
+                      static_cast<uint32_t>(len * 4), &bar[stage]);
+}
+
+// Block-size limit and minimum resident blocks of the mixed kernel: KI = 2
+// runs 3 blocks of 128 threads per SM (12 warps, <= 170 registers), KI = 1
+// 2 blocks of 256.  The compensated (hi, lo) accumulators, touched once per
+// tile, live in shared memory after the tiles: rows [18 * KI][threads].
+__host__ __device__ constexpr int mixed_max_threads(int ki) { return ki == 1 ? 256 : 128; }
+__host__ __device__ constexpr int mixed_min_blocks(int ki) { return ki == 1 ? 2 : 3; }
+
+// JU j-particles per inner iteration (2: one pair, 4: two pairs from one
+// 128-bit load per row).
+template <int KI, int JU>
+__global__ void __launch_bounds__(mixed_max_threads(KI), mixed_min_blocks(KI))
+    eval_mixed_kernel(EvalArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
-    constexpr int NC = 4;
     const int tid = threadIdx.x, lanes = a.lanes, jt = a.jtile;
     const int slot = tid / lanes, lj = tid - slot * lanes;
     const int slots = blockDim.x / lanes;
     const int ibase = blockIdx.x * slots * KI;
-    const float4 *jb = static_cast<const float4 *>(a.jb);
-    const float eps2 = static_cast<float>(a.eps2);
+    const float *jf = static_cast<const float *>(a.jb);
+    const size_t np = static_cast<size_t>(a.n);
+    const float2 eps2 = f2(static_cast<float>(a.eps2));
+    constexpr int kRow[12] = {0, 1, 2, 4, 5, 6, 7, 8, 9, 10, 11, 12};
 
     int kidx[KI];
-    float ip[KI][12];
-    float hi[9][KI], lo[9][KI], part[9][KI];
+    float2 ni[KI][12];
+    float2 part[9][KI];
+    float *acc_s = reinterpret_cast<float *>(smem) + static_cast<size_t>(2) * NCF * jt;
+    const int nthr = blockDim.x;
 #pragma unroll
     for (int k = 0; k < KI; ++k) {
         const int p = ibase + slot + k * slots;
         kidx[k] = p < a.n_act ? p : -1;
         const int i = a.act[p < a.n_act ? p : a.n_act - 1];
-        const float4 r0 = jb[i], r1 = jb[a.n + i], r2 = jb[2 * (size_t)a.n + i], r3 = jb[3 * (size_t)a.n + i];
-        ip[k][0] = r0.x; ip[k][1] = r0.y; ip[k][2] = r0.z;
-        ip[k][3] = r1.x; ip[k][4] = r1.y; ip[k][5] = r1.z;
-        ip[k][6] = r2.x; ip[k][7] = r2.y; ip[k][8] = r2.z;
-        ip[k][9] = r3.x; ip[k][10] = r3.y; ip[k][11] = r3.z;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            hi[q][k] = 0.0f;
-            lo[q][k] = 0.0f;
-        }
+        for (int q = 0; q < 12; ++q)
+            ni[k][q] = f2(-jf[kRow[q] * np + i]);
+#pragma unroll
+        for (int q = 0; q < 18; ++q)
+            acc_s[(q * KI + k) * nthr + tid] = 0.0f;
     }
 
     const int jbeg = blockIdx.y * a.jchunk;
@@ -338,7 +392,7 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_mixed_kernel(EvalArg
         nbk::mbar_init(&bar[1], 1);
         nbk::fence_mbar_init();
         for (; issued < min(2, ntiles); ++issued)
-            issue_tile<NC>(smem, bar, a, issued, jbeg + issued * jt, min(jt, jend - (jbeg + issued * jt)));
+            issue_tile_rows(smem, bar, a, issued, jbeg + issued * jt, min(jt, jend - (jbeg + issued * jt)));
     }
     __syncthreads();
 
@@ -351,35 +405,65 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_mixed_kernel(EvalArg
             return;
         }
         const int len = min(jt, jend - (jbeg + tl * jt));
-        const float4 *s = reinterpret_cast<const float4 *>(smem) + static_cast<size_t>(st) * NC * jt;
+        const float *s = reinterpret_cast<const float *>(smem) + static_cast<size_t>(st) * NCF * jt;
 #pragma unroll
         for (int k = 0; k < KI; ++k)
 #pragma unroll
             for (int q = 0; q < 9; ++q)
-                part[q][k] = 0.0f;
-        for (int jj = lj; jj < len; jj += lanes) {
-            const float4 h = s[jj], l = s[jt + jj], vv = s[2 * jt + jj], aa = s[3 * jt + jj];
+                part[q][k] = f2(0.0f);
+        for (int jj = JU * lj; jj < len; jj += JU * lanes) {
+            if (JU == 4) {
+                float2 c0[NCF], c1[NCF];
 #pragma unroll
-            for (int k = 0; k < KI; ++k) {
-                float pk[9];
+                for (int r = 0; r < NCF; ++r) {
+                    const float4 w = *reinterpret_cast<const float4 *>(s + r * jt + jj);
+                    c0[r] = make_float2(w.x, w.y);
+                    c1[r] = make_float2(w.z, w.w);
+                }
 #pragma unroll
-                for (int q = 0; q < 9; ++q)
-                    pk[q] = part[q][k];
-                pair_mixed(h, l, vv, aa, ip[k], eps2, pk);
+                for (int k = 0; k < KI; ++k) {
+                    float2 pk[9];
 #pragma unroll
-                for (int q = 0; q < 9; ++q)
-                    part[q][k] = pk[q];
+                    for (int q = 0; q < 9; ++q)
+                        pk[q] = part[q][k];
+                    pair_mixed2(c0, ni[k], eps2, pk);
+                    pair_mixed2(c1, ni[k], eps2, pk);
+#pragma unroll
+                    for (int q = 0; q < 9; ++q)
+                        part[q][k] = pk[q];
+                }
+            } else {
+                float2 c0[NCF];
+#pragma unroll
+                for (int r = 0; r < NCF; ++r)
+                    c0[r] = *reinterpret_cast<const float2 *>(s + r * jt + jj);
+#pragma unroll
+                for (int k = 0; k < KI; ++k) {
+                    float2 pk[9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q)
+                        pk[q] = part[q][k];
+                    pair_mixed2(c0, ni[k], eps2, pk);
+#pragma unroll
+                    for (int q = 0; q < 9; ++q)
+                        part[q][k] = pk[q];
+                }
             }
         }
-        // fold the FP32 tile sums into the compensated accumulators
+        // fold the FP32 tile sums (both halves) into the compensated accumulators
 #pragma unroll
         for (int k = 0; k < KI; ++k)
 #pragma unroll
-            for (int q = 0; q < 9; ++q)
-                nbk::two_sum_acc(hi[q][k], lo[q][k], part[q][k]);
+            for (int q = 0; q < 9; ++q) {
+                float h = acc_s[(q * KI + k) * nthr + tid];
+                float l = acc_s[((9 + q) * KI + k) * nthr + tid];
+                nbk::two_sum_acc(h, l, __fadd_rn(part[q][k].x, part[q][k].y));
+                acc_s[(q * KI + k) * nthr + tid] = h;
+                acc_s[((9 + q) * KI + k) * nthr + tid] = l;
+            }
         __syncthreads();
         if (tid == 0 && tl + 2 < ntiles) {
-            issue_tile<NC>(smem, bar, a, st, jbeg + (tl + 2) * jt, min(jt, jend - (jbeg + (tl + 2) * jt)));
+            issue_tile_rows(smem, bar, a, st, jbeg + (tl + 2) * jt, min(jt, jend - (jbeg + (tl + 2) * jt)));
             ++issued;
         }
     }
@@ -389,7 +473,8 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_mixed_kernel(EvalArg
     for (int k = 0; k < KI; ++k)
 #pragma unroll
         for (int q = 0; q < 9; ++q)
-            acc[q][k] = static_cast<double>(hi[q][k]) + static_cast<double>(lo[q][k]);
+            acc[q][k] = static_cast<double>(acc_s[(q * KI + k) * nthr + tid]) +
+                        static_cast<double>(acc_s[((9 + q) * KI + k) * nthr + tid]);
     for (int off = lanes >> 1; off > 0; off >>= 1)
 #pragma unroll
         for (int k = 0; k < KI; ++k)
@@ -400,7 +485,7 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_mixed_kernel(EvalArg
 }
 
 constexpr int kRecBytes64 = 5 * 16;
-constexpr int kRecBytes32 = 4 * 16;
+constexpr int kRecBytes32 = NCF * 4;
 
 template <typename K>
 cudaError_t set_smem_attr(K kernel)
@@ -418,9 +503,35 @@ cudaError_t nb_eval_smem_setup()
     if ((e = set_smem_attr(eval_fp64_kernel<1>)) != cudaSuccess) return e;
     if ((e = set_smem_attr(eval_fp64_kernel<2>)) != cudaSuccess) return e;
     if ((e = set_smem_attr(eval_fp64_kernel<4>)) != cudaSuccess) return e;
-    if ((e = set_smem_attr(eval_mixed_kernel<1>)) != cudaSuccess) return e;
-    if ((e = set_smem_attr(eval_mixed_kernel<2>)) != cudaSuccess) return e;
-    return set_smem_attr(eval_mixed_kernel<4>);
+    if ((e = set_smem_attr(eval_mixed_kernel<1, 2>)) != cudaSuccess) return e;
+    if ((e = set_smem_attr(eval_mixed_kernel<1, 4>)) != cudaSuccess) return e;
+    if ((e = set_smem_attr(eval_mixed_kernel<2, 2>)) != cudaSuccess) return e;
+    return set_smem_attr(eval_mixed_kernel<2, 4>);
+}
+
+// Blocks of the chosen evaluation kernel that fit on one SM.
+int resident_blocks(const nb_ctx *c, const nb_tiles &t)
+{
+    const bool mixed = c->cfg.precision == NB_MIXED;
+    const size_t smem = static_cast<size_t>(2) * (mixed ? kRecBytes32 : kRecBytes64) * t.jtile +
+                        (mixed ? static_cast<size_t>(18) * t.ki * t.threads * sizeof(float) : 0);
+    int nb = 0;
+    cudaError_t e;
+    if (mixed) {
+        if (t.ki == 1 && t.junroll == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_mixed_kernel<1, 2>, t.threads, smem);
+        else if (t.ki == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_mixed_kernel<1, 4>, t.threads, smem);
+        else if (t.junroll == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_mixed_kernel<2, 2>, t.threads, smem);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_mixed_kernel<2, 4>, t.threads, smem);
+    } else {
+        if (t.ki == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_fp64_kernel<1>, t.threads, smem);
+        else if (t.ki == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_fp64_kernel<2>, t.threads, smem);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_fp64_kernel<4>, t.threads, smem);
+    }
+    if (e != cudaSuccess || nb < 1) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    return nb;
 }
 
 // Automatic launch shape.  Large active sets: one i per thread slot, no
@@ -431,10 +542,16 @@ nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req)
 {
     nb_tiles t = req;
     const bool mixed = c->cfg.precision == NB_MIXED;
-    if (t.threads <= 0)
-        t.threads = 128;
+    // defaults from the launch-shape sweep on GB300 (autotune.py): mixed
+    // KI = 2 with four j per iteration; larger blocks and tiles once the
+    // active set fills the grid without splitting
+    const bool big = n_act >= 16384;
     if (t.ki <= 0)
         t.ki = mixed ? 2 : 1;
+    if (t.threads <= 0)
+        t.threads = mixed ? mixed_max_threads(t.ki) : 128;
+    if (t.junroll <= 0)
+        t.junroll = 4;
     if (t.lanes <= 0) {
         int l = 1;
         while (l < 32 && static_cast<int64_t>(t.threads / (2 * l)) * t.ki >= n_act)
@@ -442,17 +559,35 @@ nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req)
         t.lanes = l;
     }
     if (t.jtile <= 0)
-        t.jtile = mixed ? 256 : 128;
-    if (t.jtile % t.lanes)
-        t.jtile = (t.jtile / t.lanes + 1) * t.lanes;
+        t.jtile = mixed ? (big ? 512 : 256) : 256;
+    if (mixed && t.jtile % 4)
+        t.jtile = (t.jtile / 4 + 1) * 4;   // whole 16-byte rows per bulk copy
     if (t.split <= 0) {
+        // Split the j-range so that the grid fills whole waves of resident
+        // blocks: all blocks of a launch do equal work, so a partial last
+        // wave idles the rest of the GPU for a whole block's duration.
+        const int64_t jn = mixed ? c->npad : c->n;
         const int64_t itile = static_cast<int64_t>(t.threads / t.lanes) * t.ki;
         const int64_t nblk = (n_act + itile - 1) / itile;
-        const int64_t target = static_cast<int64_t>(c->sm_count) * 4;
-        int64_t s = nblk >= target ? 1 : (target + nblk - 1) / nblk;
-        const int64_t max_s = std::max<int64_t>(1, c->n / (2 * t.jtile));
-        s = std::min<int64_t>(std::min<int64_t>(s, max_s), 1024);
-        t.split = static_cast<int32_t>(std::max<int64_t>(1, s));
+        const int64_t cap = static_cast<int64_t>(c->sm_count) * resident_blocks(c, t);
+        const int64_t max_s = std::max<int64_t>(1, std::min<int64_t>(1024, jn / (2 * t.jtile)));
+        int64_t best = 1;
+        if (nblk < 2 * cap) {
+            double best_eff = -1.0;
+            for (int64_t s = 1; s <= max_s; ++s) {
+                const int64_t blocks = nblk * s;
+                const int64_t waves = (blocks + cap - 1) / cap;
+                const double eff = static_cast<double>(blocks) / static_cast<double>(waves * cap);
+                // prefer fuller waves; among near-equal ones the fewer splits
+                if (eff > best_eff + 0.02) {
+                    best_eff = eff;
+                    best = s;
+                }
+                if (blocks >= 4 * cap)
+                    break;
+            }
+        }
+        t.split = static_cast<int32_t>(best);
     }
     return t;
 }
@@ -462,25 +597,29 @@ cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L)
     const nb_tiles &t = L.tiles;
     if (L.n_act <= 0)
         return cudaSuccess;
-    if (!(t.ki == 1 || t.ki == 2 || t.ki == 4) || t.threads < 32 || t.threads > max_threads_for(t.ki) ||
-        t.threads % 32 || !is_pow2(t.lanes) || t.lanes > 32 || t.jtile < t.lanes ||
-        t.jtile % t.lanes || t.split < 1)
-        return cudaErrorInvalidValue;
     const bool mixed = c->cfg.precision == NB_MIXED;
+    if (!(t.ki == 1 || t.ki == 2 || (t.ki == 4 && !mixed)) || t.threads < 32 ||
+        t.threads > (mixed ? mixed_max_threads(t.ki) : max_threads_for(t.ki)) || t.threads % 32 ||
+        !is_pow2(t.lanes) || t.lanes > 32 || t.jtile < 1 || t.split < 1)
+        return cudaErrorInvalidValue;
+    if (mixed && (!(t.junroll == 2 || t.junroll == 4) || t.jtile % 4))
+        return cudaErrorInvalidValue;
     const int rec = mixed ? kRecBytes32 : kRecBytes64;
-    const size_t smem = static_cast<size_t>(2) * rec * t.jtile;
+    const size_t smem = static_cast<size_t>(2) * rec * t.jtile +
+                        (mixed ? static_cast<size_t>(18) * t.ki * t.threads * sizeof(float) : 0);
     if (smem > 200 * 1024)
         return cudaErrorInvalidValue;
     const int itile = (t.threads / t.lanes) * t.ki;
     const int gx = (L.n_act + itile - 1) / itile;
     // j chunk per split, a whole number of tiles
-    int64_t chunk = (c->n + t.split - 1) / t.split;
+    const int64_t jn = mixed ? c->npad : c->n;
+    int64_t chunk = (jn + t.split - 1) / t.split;
     chunk = (chunk + t.jtile - 1) / t.jtile * t.jtile;
-    const int split = static_cast<int>((c->n + chunk - 1) / chunk);
+    const int split = static_cast<int>((jn + chunk - 1) / chunk);
 
     EvalArgs a;
-    a.jb = mixed ? static_cast<const void *>(c->jb32) : static_cast<const void *>(c->jb64);
-    a.n = static_cast<int>(c->n);
+    a.jb = mixed ? static_cast<const void *>(c->jf32) : static_cast<const void *>(c->jb64);
+    a.n = static_cast<int>(jn);
     a.act = L.act;
     a.n_act = L.n_act;
     a.out = L.out;
@@ -521,9 +660,10 @@ cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L)
     }
     const dim3 grid(gx, split), block(t.threads);
     if (mixed) {
-        if (t.ki == 1) eval_mixed_kernel<1><<<grid, block, smem, c->stream>>>(a);
-        else if (t.ki == 2) eval_mixed_kernel<2><<<grid, block, smem, c->stream>>>(a);
-        else eval_mixed_kernel<4><<<grid, block, smem, c->stream>>>(a);
+        if (t.ki == 1 && t.junroll == 2) eval_mixed_kernel<1, 2><<<grid, block, smem, c->stream>>>(a);
+        else if (t.ki == 1) eval_mixed_kernel<1, 4><<<grid, block, smem, c->stream>>>(a);
+        else if (t.junroll == 2) eval_mixed_kernel<2, 2><<<grid, block, smem, c->stream>>>(a);
+        else eval_mixed_kernel<2, 4><<<grid, block, smem, c->stream>>>(a);
     } else {
         if (t.ki == 1) eval_fp64_kernel<1><<<grid, block, smem, c->stream>>>(a);
         else if (t.ki == 2) eval_fp64_kernel<2><<<grid, block, smem, c->stream>>>(a);

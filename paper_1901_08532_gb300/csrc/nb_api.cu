@@ -69,7 +69,7 @@ std::string check_config(const nb_config &c)
     if (c.dt_shared != 0.0 && !is_pow2_double(c.dt_shared))
         return "dt_shared must be 0 or a power of two";
     const nb_tiles &t = c.tiles;
-    if (t.ki < 0 || t.threads < 0 || t.jtile < 0 || t.lanes < 0 || t.split < 0)
+    if (t.ki < 0 || t.threads < 0 || t.jtile < 0 || t.lanes < 0 || t.split < 0 || t.junroll < 0)
         return "tile fields must be >= 0";
     return "";
 }
@@ -86,6 +86,8 @@ std::string check_tiles(const nb_tiles &t)
         return "tiles.jtile must be in [0, 4096]";
     if (t.split < 0 || t.split > 4096)
         return "tiles.split must be in [0, 4096]";
+    if (t.junroll != 0 && t.junroll != 2 && t.junroll != 4)
+        return "tiles.junroll must be 0, 2 or 4";
     return "";
 }
 
@@ -167,7 +169,7 @@ void free_all(nb_ctx *c)
     cudaFree(c->t);
     cudaFree(c->dt);
     cudaFree(c->jb64);
-    cudaFree(c->jb32);
+    cudaFree(c->jf32);
     cudaFree(c->act);
     cudaFree(c->anew);
     cudaFree(c->stage);
@@ -281,9 +283,11 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x, con
     CUI(cudaMalloc(&c->st, 18 * N * sizeof(double)));
     CUI(cudaMalloc(&c->t, N * sizeof(double)));
     CUI(cudaMalloc(&c->dt, N * sizeof(double)));
-    if (cf.precision == NB_MIXED)
-        CUI(cudaMalloc(&c->jb32, 4 * N * sizeof(float4)));
-    else
+    c->npad = (n + 3) / 4 * 4;
+    if (cf.precision == NB_MIXED) {
+        CUI(cudaMalloc(&c->jf32, 13 * static_cast<size_t>(c->npad) * sizeof(float)));
+        CUI(cudaMemsetAsync(c->jf32, 0, 13 * static_cast<size_t>(c->npad) * sizeof(float), c->stream));
+    } else
         CUI(cudaMalloc(&c->jb64, 5 * N * sizeof(double2)));
     CUI(cudaMalloc(&c->act, N * sizeof(int32_t)));
     CUI(cudaMalloc(&c->anew, 9 * N * sizeof(double)));
@@ -352,20 +356,16 @@ nb_status nb_get_predicted(nb_ctx *c, double *xp, double *vp, double *ap)
         return fail(c, NB_ESTATE, "nb_get_predicted needs a prediction (nb_predict) first");
     const size_t N = static_cast<size_t>(c->n);
     if (c->cfg.precision == NB_MIXED) {
-        std::vector<float4> h(4 * N);
-        CU(c, cudaMemcpyAsync(h.data(), c->jb32, 4 * N * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+        const size_t P = static_cast<size_t>(c->npad);
+        std::vector<float> h(13 * P);
+        CU(c, cudaMemcpyAsync(h.data(), c->jf32, 13 * P * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
         CU(c, cudaStreamSynchronize(c->stream));
-        for (size_t i = 0; i < N; ++i) {
-            const float4 hi = h[i], lo = h[N + i], vv = h[2 * N + i], aa = h[3 * N + i];
-            const double px[3] = {(double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y,
-                                  (double)hi.z + (double)lo.z};
-            const double pv[3] = {vv.x, vv.y, vv.z}, pa[3] = {aa.x, aa.y, aa.z};
+        for (size_t i = 0; i < N; ++i)
             for (int d = 0; d < 3; ++d) {
-                if (xp) xp[3 * i + d] = px[d];
-                if (vp) vp[3 * i + d] = pv[d];
-                if (ap) ap[3 * i + d] = pa[d];
+                if (xp) xp[3 * i + d] = (double)h[d * P + i] + (double)h[(4 + d) * P + i];
+                if (vp) vp[3 * i + d] = h[(7 + d) * P + i];
+                if (ap) ap[3 * i + d] = h[(10 + d) * P + i];
             }
-        }
         return NB_OK;
     }
     std::vector<double2> h(5 * N);

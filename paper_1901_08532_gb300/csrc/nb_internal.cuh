@@ -16,9 +16,10 @@
 //   st[(F * 3 + k) * n + i] for field F in {X, V, A, J, S, C}, component k.
 // Evaluation buffers written by the predictor (stride n):
 //   FP64:  jb64[c * n + i], c = 0..4: (x, y) (z, m) (vx, vy) (vz, ax) (ay, az)
-//   mixed: jb32[c * n + i], c = 0..3: (xh, yh, zh, m) (xl, yl, zl, 0)
-//                                      (vx, vy, vz, 0) (ax, ay, az, 0)
-//          with xh = fp32(x), xl = fp32(x - xh).
+//   mixed: jf32[c * npad + i], 13 float rows c = 0..12:
+//          xh yh zh m xl yl zl vx vy vz ax ay az, with xh = fp32(x) and
+//          xl = fp32(x - xh); npad = n rounded up to a multiple of 4, the
+//          padding rows hold zero-mass particles (contribute exactly 0).
 // Evaluation output (stride ostride): out[q * ostride + k], q = 0..8 for
 //   acc x,y,z, jerk x,y,z, snap x,y,z of the k-th listed particle.
 enum { F_X = 0, F_V = 1, F_A = 2, F_J = 3, F_S = 4, F_C = 5, NFIELD = 6 };
@@ -45,7 +46,8 @@ struct nb_ctx {
     double *t = nullptr;       // [n]
     double *dt = nullptr;      // [n]
     double2 *jb64 = nullptr;   // [5][n]
-    float4 *jb32 = nullptr;    // [4][n]
+    float *jf32 = nullptr;     // [13][npad]
+    int64_t npad = 0;
     int32_t *act = nullptr;    // [n]
     double *anew = nullptr;    // [9][n]
     double *stage = nullptr;   // [3][n][3] output staging

@@ -24,6 +24,8 @@ SHAPES = [
     {"ki": 1, "threads": 32, "jtile": 64, "lanes": 32, "split": 7},
     {"ki": 4, "threads": 128, "jtile": 256, "lanes": 2, "split": 2},
     {"ki": 2, "threads": 256, "jtile": 32, "lanes": 8, "split": 1},
+    {"ki": 1, "threads": 128, "jtile": 512, "lanes": 1, "split": 1, "junroll": 2},
+    {"ki": 2, "threads": 128, "jtile": 60, "lanes": 1, "split": 5, "junroll": 4},
 ]
 
 
@@ -33,8 +35,19 @@ def _system(n, seed, imf="equal"):
     return m, x, v, a
 
 
+def _shape_for(prec, shape):
+    """The mixed kernel takes KI 1 or 2 (at most 128 threads for KI 2); KI 4
+    shapes run there as KI 2 with two j per inner iteration."""
+    shape = dict(shape)
+    if prec == 1 and shape.get("ki") == 4:
+        shape.update(ki=2, junroll=2)
+    if prec == 1 and shape.get("ki") == 2 and shape.get("threads", 0) > 128:
+        shape.update(threads=128)
+    return shape
+
+
 def _gpu_eval(nb, prec, m, x, v, a, eps, active, shape):
-    g = nb.NBody(m, x, v, eps, precision=prec, tiles=shape, start_forces=False)
+    g = nb.NBody(m, x, v, eps, precision=prec, tiles=_shape_for(prec, shape), start_forces=False)
     n = m.size
     g.set_state({"x": x, "v": v, "a": a, "j": np.zeros((n, 3)), "s": np.zeros((n, 3)),
                  "c": np.zeros((n, 3)), "t": np.zeros(n), "dt": np.full(n, 2.0 ** -3)})

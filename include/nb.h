@@ -193,6 +193,53 @@ nb_status nb_resolve_tiles(nb_ctx *ctx, int64_t n_act, nb_tiles *out);
  * interactions evaluated (n_act * n per evaluation, self term included). */
 nb_status nb_counters(nb_ctx *ctx, int64_t *launches, double *interactions);
 
+/* ---------------------------------------------------------------------------
+ * Ensembles: many independent systems, each on its own block time steps,
+ * advanced together in ONE persistent GPU launch (captured in a CUDA graph).
+ * The paper integrates one system; this is the batched form of the same
+ * predictor / evaluation / corrector cycle (sections 2-3).  Each system is
+ * owned by a cluster of ctas_per_system thread blocks that pull systems from
+ * a device queue, largest first.
+ * ------------------------------------------------------------------------- */
+typedef struct nb_ensemble nb_ensemble;
+
+/* n_systems systems of sizes[] particles; m, x ([.][3]) and v ([.][3]) are
+ * the systems' particles concatenated in order (host, copied).  Same config
+ * fields as nb_init (tiles and start_forces are ignored; the starting forces
+ * and steps are always computed, in one launch).  The ensemble runs on
+ * cfg->stream, or on a stream of its own when that is NULL (graph capture
+ * needs a stream other than the legacy default stream).
+ * Errors: NB_EINVAL, NB_ENONFINITE, NB_ENOMEM, NB_ECUDA. */
+nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *sizes,
+                           const double *m, const double *x, const double *v, double eps,
+                           const nb_config *cfg);
+
+/* Launch shape: thread blocks per system (1..8, one hardware cluster),
+ * threads per block (64..256, multiple of 32), j-tile length (multiple of 4). */
+nb_status nb_ensemble_set_shape(nb_ensemble *e, int32_t ctas_per_system, int32_t threads,
+                                int32_t jtile);
+
+/* Advance every system with block steps until all of its particles reach
+ * t_end (a multiple of dt_max, or of dt_shared in shared mode), in one
+ * persistent launch; with use_graph != 0 the launch is captured once in a
+ * CUDA graph and replayed on later calls with the same t_end.  Synchronises. */
+nb_status nb_ensemble_run(nb_ensemble *e, double t_end, int use_graph);
+
+/* State of all particles, systems concatenated as at nb_ensemble_init. */
+nb_status nb_ensemble_get_state(nb_ensemble *e, double *x, double *v, double *a, double *j,
+                                double *s, double *c, double *t, double *dt);
+
+/* Block steps of each system in the last run (steps[n_systems], may be
+ * NULL), pair interactions evaluated since creation, and launches issued. */
+nb_status nb_ensemble_stats(nb_ensemble *e, int64_t *steps, double *interactions,
+                            int64_t *launches);
+
+/* Message for the last error of e (NULL: the last failed nb_ensemble_init
+ * on this thread). */
+const char *nb_ensemble_last_error(const nb_ensemble *e);
+
+void nb_ensemble_free(nb_ensemble *e);
+
 /* Allocation-free FP64 evaluation.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory: a host
  * application that owns all GPU memory through its own pool or caching

@@ -79,6 +79,19 @@ _lib.nb_counters.argtypes = [_vp, _i64, _d]
 _lib.nb_evaluate_fp64_static.argtypes = [_vp, C.c_int64, _vp, C.c_int64, C.c_double, C.c_int32,
                                          _vp, _vp]
 _lib.nb_evaluate_fp64_static.restype = C.c_int
+_lib.nb_ensemble_init.argtypes = [C.POINTER(C.c_void_p), C.c_int32, _i64, _d, _d, _d, C.c_double,
+                                  C.POINTER(Config)]
+_lib.nb_ensemble_set_shape.argtypes = [_vp, C.c_int32, C.c_int32, C.c_int32]
+_lib.nb_ensemble_run.argtypes = [_vp, C.c_double, C.c_int]
+_lib.nb_ensemble_get_state.argtypes = [_vp] + [_d] * 8
+_lib.nb_ensemble_stats.argtypes = [_vp, _i64, _d, _i64]
+_lib.nb_ensemble_last_error.argtypes = [_vp]
+_lib.nb_ensemble_last_error.restype = C.c_char_p
+_lib.nb_ensemble_free.argtypes = [_vp]
+_lib.nb_ensemble_free.restype = None
+for _f in ("nb_ensemble_init", "nb_ensemble_set_shape", "nb_ensemble_run", "nb_ensemble_get_state",
+           "nb_ensemble_stats"):
+    getattr(_lib, _f).restype = C.c_int
 _lib.nb_last_error.argtypes = [_vp]
 _lib.nb_last_error.restype = C.c_char_p
 _lib.nb_free.argtypes = [_vp]
@@ -91,7 +104,9 @@ for _f in ("nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_corre
 EXPORTED = ("nb_config_default", "nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_correct", "nb_step",
             "nb_run_until", "nb_energy", "nb_angmom", "nb_get_state", "nb_set_state",
             "nb_get_active", "nb_set_tiles", "nb_resolve_tiles", "nb_counters",
-            "nb_evaluate_fp64_static", "nb_last_error", "nb_free")
+            "nb_evaluate_fp64_static", "nb_last_error", "nb_free", "nb_ensemble_init",
+            "nb_ensemble_set_shape", "nb_ensemble_run", "nb_ensemble_get_state", "nb_ensemble_stats",
+            "nb_ensemble_last_error", "nb_ensemble_free")
 
 
 def lib():
@@ -286,3 +301,73 @@ class NBody:
         it = C.c_double()
         self._check(_lib.nb_counters(self._ctx, C.byref(la), C.byref(it)))
         return int(la.value), float(it.value)
+
+
+class Ensemble:
+    """Independent systems advanced together in one persistent launch.
+
+    sizes: particle count of each system; m, x, v: the systems' particles
+    concatenated (host arrays).  Same precision/step parameters as NBody.
+    """
+
+    def __init__(self, sizes, m, x, v, eps, precision=NB_FP64, eta=0.4, eta_s=0.01,
+                 dt_min=2.0 ** -20, dt_max=2.0 ** -3, dt_shared=0.0, stream=None):
+        sizes = np.ascontiguousarray(sizes, dtype=np.int64)
+        m = _f64(m)
+        n = m.size
+        assert sizes.sum() == n
+        x, v = _f64(x, (n, 3)), _f64(v, (n, 3))
+        cfg = Config()
+        _lib.nb_config_default(C.byref(cfg))
+        cfg.precision, cfg.eta, cfg.eta_s = precision, eta, eta_s
+        cfg.dt_min, cfg.dt_max, cfg.dt_shared = dt_min, dt_max, dt_shared
+        if stream is not None:
+            cfg.stream = _stream_handle(stream)
+        self.sizes = sizes
+        self.n = n
+        self.precision = precision
+        self._e = C.c_void_p()
+        st = _lib.nb_ensemble_init(C.byref(self._e), sizes.size, sizes.ctypes.data_as(_i64), _ptr(m),
+                                   _ptr(x), _ptr(v), float(eps), C.byref(cfg))
+        if st != NB_OK:
+            raise NBError(st, _lib.nb_ensemble_last_error(None).decode())
+
+    def _check(self, st):
+        if st != NB_OK:
+            raise NBError(st, _lib.nb_ensemble_last_error(self._e).decode())
+
+    def set_shape(self, ctas_per_system=8, threads=256, jtile=None):
+        if jtile is None:
+            jtile = 256 if self.precision == NB_MIXED else 128
+        self._check(_lib.nb_ensemble_set_shape(self._e, int(ctas_per_system), int(threads), int(jtile)))
+
+    def run(self, t_end, use_graph=True):
+        self._check(_lib.nb_ensemble_run(self._e, float(t_end), 1 if use_graph else 0))
+
+    def state(self):
+        n = self.n
+        out = {k: np.zeros((n, 3)) for k in ("x", "v", "a", "j", "s", "c")}
+        out["t"] = np.zeros(n)
+        out["dt"] = np.zeros(n)
+        self._check(_lib.nb_ensemble_get_state(self._e, *[_ptr(out[k]) for k in
+                                                          ("x", "v", "a", "j", "s", "c", "t", "dt")]))
+        return out
+
+    def stats(self):
+        steps = np.zeros(self.sizes.size, dtype=np.int64)
+        it = C.c_double()
+        la = C.c_int64()
+        self._check(_lib.nb_ensemble_stats(self._e, steps.ctypes.data_as(_i64), C.byref(it),
+                                           C.byref(la)))
+        return steps, float(it.value), int(la.value)
+
+    def close(self):
+        if getattr(self, "_e", None) and self._e.value:
+            _lib.nb_ensemble_free(self._e)
+            self._e = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -8,34 +8,12 @@
 //     eta (A1 / A4)^(1/3), A_k = sqrt(|a^(k-1)| |a^(k+1)|) + |a^(k)|,
 //     rounded down to a power of two, clamped to [dt_min, dt_max], at most
 //     doubled, and doubled only where t1 is a multiple of the doubled step.
+#include "nb_device.cuh"
 #include "nb_internal.cuh"
 
 namespace {
 
-// Largest power of two <= x for positive normal x (clears the mantissa).
-__device__ __forceinline__ double pow2_floor(double x)
-{
-    return __hiloint2double(__double2hiint(x) & 0x7ff00000, 0);
-}
-
-__device__ double quantise(double crit, double dt_old, double t1, double dt_min, double dt_max,
-                           bool *floor_hit)
-{
-    double p;
-    *floor_hit = false;
-    if (!(crit >= dt_min)) {
-        *floor_hit = true;
-        p = dt_min;
-    } else {
-        p = isinf(crit) ? dt_max : fmin(pow2_floor(crit), dt_max);
-    }
-    if (dt_old > 0.0 && p > dt_old) {
-        const double d2 = 2.0 * dt_old;
-        const double q = t1 * (1.0 / d2);  // exact: d2 is a power of two
-        p = (q == trunc(q)) ? d2 : dt_old;
-    }
-    return p;
-}
+using nbk::quantise;
 
 struct CorrectArgs {
     double *st;
@@ -69,23 +47,12 @@ __global__ void __launch_bounds__(128) correct_kernel(CorrectArgs a)
         double *pj = a.st + (F_J * 3 + d) * N + i;
         double *ps = a.st + (F_S * 3 + d) * N + i;
         double *pc = a.st + (F_C * 3 + d) * N + i;
-        const double x0 = *px, v0 = *pv, a0 = *pa, j0 = *pj, s0 = *ps;
+        const double a0 = *pa, j0 = *pj, s0 = *ps;
         const double a1 = a.anew[(0 + d) * (size_t)a.ostride + k];
         const double j1 = a.anew[(3 + d) * (size_t)a.ostride + k];
         const double s1 = a.anew[(6 + d) * (size_t)a.ostride + k];
-        const double v1 =
-            fma(h, fma(h, fma(h, (s0 + s1) * (1.0 / 120.0), -(j1 - j0) * 0.1), 0.5 * (a0 + a1)), v0);
-        const double x1 =
-            fma(h, fma(h, fma(h, (j0 + j1) * (1.0 / 120.0), -(a1 - a0) * 0.1), 0.5 * (v0 + v1)), x0);
-        // quintic through (a, j, s) at both ends: residuals of the cubic
-        // Taylor part, then the inverse of the 3x3 Hermite system
-        const double R1 = a1 - fma(h, fma(0.5 * h, s0, j0), a0);
-        const double R2 = h * (j1 - fma(h, s0, j0));
-        const double R3 = h * h * (s1 - s0);
-        const double ih3 = ih * ih * ih;
-        const double c1 = (60.0 * R1 - 36.0 * R2 + 9.0 * R3) * ih3;
-        const double d1 = (360.0 * R1 - 192.0 * R2 + 36.0 * R3) * ih3 * ih;
-        const double e1 = (720.0 * R1 - 360.0 * R2 + 60.0 * R3) * ih3 * ih * ih;
+        const nbk::Corrected r = nbk::hermite_correct(h, ih, *px, *pv, a0, j0, s0, a1, j1, s1);
+        const double x1 = r.x1, v1 = r.v1, c1 = r.c1, d1 = r.d1, e1 = r.e1;
         finite = finite && isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1) &&
                  isfinite(s1) && isfinite(c1);
         *px = x1;
@@ -107,9 +74,7 @@ __global__ void __launch_bounds__(128) correct_kernel(CorrectArgs a)
     if (a.dt_shared > 0.0) {
         dtn = a.dt_shared;
     } else {
-        const double A1 = sqrt(sqrt(n2[0]) * sqrt(n2[2])) + sqrt(n2[1]);
-        const double A4 = sqrt(sqrt(n2[3]) * sqrt(n2[5])) + sqrt(n2[4]);
-        dtn = quantise(a.eta * cbrt(A1 / A4), a.dt[i], a.t1, a.dt_min, a.dt_max, &hit);
+        dtn = quantise(nbk::aarseth_dt(n2, a.eta), a.dt[i], a.t1, a.dt_min, a.dt_max, &hit);
     }
     a.dt[i] = dtn;
     if (hit)

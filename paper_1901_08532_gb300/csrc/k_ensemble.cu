@@ -1,0 +1,960 @@
+// Ensemble of independent N-body systems, each on its own block time steps
+// (paper, sections 2-3: block steps, predictor / evaluation / corrector),
+// advanced together in ONE persistent launch.
+//
+// Work division on GB300: the grid is made of thread-block clusters of G
+// CTAs (G <= 8, co-scheduled by the hardware).  Each hardware cluster takes
+// the next system from an atomic queue (largest systems first) and runs its
+// whole block-step loop to t_end:
+//   schedule  t_next = min(t_i + dt_i) over the system; active set in
+//             ascending order (each CTA scans its slice, sums across the
+//             cluster through distributed shared memory);
+//   predict   each CTA its slice, into the system's evaluation buffer;
+//   evaluate  each CTA a share of the active particles against all of the
+//             system's particles, j-tiles by TMA bulk copy into shared memory;
+//   correct   each CTA the particles it evaluated.
+// Phases are separated by the cluster barrier (a hardware barrier with
+// release/acquire semantics at cluster scope, no flag spinning).  Systems are
+// independent, so no grid-wide synchronisation exists.  The only waits that
+// poll (TMA completion) give up after a time limit; a failure is made
+// uniform across the cluster and ends the launch with an error flag.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "nb_device.cuh"
+#include "nb_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+struct nb_ensemble {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    nb_config cfg{};
+    double eps = 0;
+    int nc = 0;
+    int64_t P = 0;  // padded particle total
+    std::vector<int32_t> off, cnt;
+    int32_t *d_off = nullptr, *d_cnt = nullptr, *d_order = nullptr;
+    double *m = nullptr, *st = nullptr, *t = nullptr, *dt = nullptr, *anew = nullptr;
+    double2 *jb64 = nullptr;
+    float *jf32 = nullptr;
+    int32_t *act = nullptr;
+    int *queue = nullptr;
+    int64_t *steps = nullptr;
+    unsigned long long *inter = nullptr;
+    nb_ctl *ctl = nullptr, *ctl_h = nullptr;
+    int G = 8, threads = 256, jtile = 256;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double graph_t_end = -1.0;
+    int64_t launches = 0;
+    bool dead = false;
+    std::string err;
+};
+
+namespace {
+
+using namespace nbk;
+
+struct EnsArgs {
+    int nc;
+    const int32_t *off, *cnt, *order;
+    int P;
+    double *st, *t, *dt;
+    const double *m;
+    double2 *jb64;
+    float *jf32;
+    int32_t *act;
+    double *anew;
+    int *queue;
+    int64_t *steps;
+    unsigned long long *inter;
+    nb_ctl *ctl;
+    double t_end, eps2, eta, eta_s, dt_min, dt_max, dt_shared;
+    int mode;  // 0: block steps to t_end, 1: start-up (a, jerk, snap, starting steps)
+    int jtile;
+};
+
+constexpr int kEnsThreads = 256;
+
+__device__ __forceinline__ double block_min(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0)
+        red[w] = v;
+    __syncthreads();
+    double r = red[0];
+    for (int q = 1; q < static_cast<int>(blockDim.x >> 5); ++q)
+        r = fmin(r, red[q]);
+    return r;
+}
+
+// Ordered compaction of the due particles of [lo, hi): each thread takes a
+// contiguous chunk, so a block-wide exclusive scan keeps index order.
+__device__ int count_due(const EnsArgs &a, int lo, int hi, double tn, int &mine, int &first)
+{
+    const int T = blockDim.x;
+    const int len = hi - lo;
+    const int per = (len + T - 1) / T;
+    first = lo + threadIdx.x * per;
+    const int last = min(hi, first + per);
+    int c = 0;
+    for (int i = first; i < last; ++i)
+        c += (a.t[i] + a.dt[i] == tn) ? 1 : 0;
+    mine = c;
+    return c;
+}
+
+__device__ int block_exclusive_scan(int v, int *red, int *total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += u;
+    }
+    __syncthreads();
+    if (lane == 31)
+        red[w] = incl;
+    __syncthreads();
+    int base = 0, tot = 0;
+    for (int q = 0; q < nw; ++q) {
+        if (q < w)
+            base += red[q];
+        tot += red[q];
+    }
+    *total = tot;
+    return base + incl - v;
+}
+
+template <bool MIXED>
+__device__ void predict_slice(const EnsArgs &a, int lo, int hi, double tp)
+{
+    const size_t P = static_cast<size_t>(a.P);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double d = tp - a.t[i];
+        Taylor p[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            p[k] = taylor(a.st[(F_X * 3 + k) * P + i], a.st[(F_V * 3 + k) * P + i],
+                          a.st[(F_A * 3 + k) * P + i], a.st[(F_J * 3 + k) * P + i],
+                          a.st[(F_S * 3 + k) * P + i], a.st[(F_C * 3 + k) * P + i], d);
+        if (MIXED) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float h = __double2float_rn(p[k].x);
+                a.jf32[k * P + i] = h;
+                a.jf32[(4 + k) * P + i] = __double2float_rn(p[k].x - static_cast<double>(h));
+                a.jf32[(7 + k) * P + i] = __double2float_rn(p[k].v);
+                a.jf32[(10 + k) * P + i] = __double2float_rn(p[k].a);
+            }
+            a.jf32[3 * P + i] = __double2float_rn(a.m[i]);
+        } else {
+            a.jb64[i] = make_double2(p[0].x, p[1].x);
+            a.jb64[P + i] = make_double2(p[2].x, a.m[i]);
+            a.jb64[2 * P + i] = make_double2(p[0].v, p[1].v);
+            a.jb64[3 * P + i] = make_double2(p[2].v, p[0].a);
+            a.jb64[4 * P + i] = make_double2(p[1].a, p[2].a);
+        }
+    }
+    // the evaluation reads this buffer through TMA (async proxy)
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+template <bool MIXED>
+__device__ __forceinline__ void issue_ens_tile(const EnsArgs &a, unsigned char *smem, uint64_t *bar,
+                                               int stage, int j0, int len)
+{
+    const int jt = a.jtile;
+    const size_t P = static_cast<size_t>(a.P);
+    if (MIXED) {
+        float *dst = reinterpret_cast<float *>(smem) + static_cast<size_t>(stage) * NCF * jt;
+        mbar_expect_tx(&bar[stage], static_cast<uint32_t>(NCF * len * 4));
+#pragma unroll
+        for (int r = 0; r < NCF; ++r)
+            bulk_g2s(dst + r * jt, a.jf32 + r * P + j0, static_cast<uint32_t>(len * 4), &bar[stage]);
+    } else {
+        double2 *dst = reinterpret_cast<double2 *>(smem) + static_cast<size_t>(stage) * 5 * jt;
+        mbar_expect_tx(&bar[stage], static_cast<uint32_t>(5 * len * 16));
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+            bulk_g2s(dst + r * jt, a.jb64 + r * P + j0, static_cast<uint32_t>(len * 16), &bar[stage]);
+    }
+}
+
+// Evaluate active slots [s0, s1) of the system starting at `off` against its
+// nj j-records.  Returns false if a TMA wait timed out (uniform in the CTA).
+template <bool MIXED>
+__device__ bool eval_share(const EnsArgs &a, int off, int nj, int s0, int s1, unsigned char *smem,
+                           uint64_t *bar, unsigned &seq)
+{
+    const int T = blockDim.x, tid = threadIdx.x, jt = a.jtile;
+    const int m = s1 - s0;
+    if (m <= 0)
+        return true;
+    const size_t P = static_cast<size_t>(a.P);
+    int lanes = 1;
+    while (lanes < 32 && (T / (2 * lanes)) >= m)
+        lanes *= 2;
+    const int slots = T / lanes, slot = tid / lanes, lj = tid - slot * lanes;
+    const int ntiles = (nj + jt - 1) / jt;
+    constexpr int kRow[12] = {0, 1, 2, 4, 5, 6, 7, 8, 9, 10, 11, 12};
+    // the j-records were written by other blocks of the cluster (generic
+    // stores, then the cluster barrier); order them before the bulk copies
+    if (tid == 0)
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+
+    for (int ib = s0; ib < s1; ib += slots) {
+        const int p = ib + slot;
+        const bool valid = p < s1;
+        const int i = a.act[off + (valid ? p : s1 - 1)];
+        double acc[9];
+        for (int q = 0; q < 9; ++q)
+            acc[q] = 0.0;
+        // i-particle data (the same predicted records the j-loop reads)
+        float2 ni[12];
+        float hi[9], lo[9];
+        double xi = 0, yi = 0, zi = 0, vxi = 0, vyi = 0, vzi = 0, axi = 0, ayi = 0, azi = 0;
+        if (MIXED) {
+#pragma unroll
+            for (int q = 0; q < 12; ++q)
+                ni[q] = f2(-a.jf32[kRow[q] * P + i]);
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                hi[q] = lo[q] = 0.0f;
+        } else {
+            const double2 r0 = a.jb64[i], r1 = a.jb64[P + i], r2 = a.jb64[2 * P + i];
+            const double2 r3 = a.jb64[3 * P + i], r4 = a.jb64[4 * P + i];
+            xi = r0.x; yi = r0.y; zi = r1.x;
+            vxi = r2.x; vyi = r2.y; vzi = r3.x;
+            axi = r3.y; ayi = r4.x; azi = r4.y;
+        }
+        if (tid == 0)
+            for (int q = 0; q < min(2, ntiles); ++q)
+                issue_ens_tile<MIXED>(a, smem, bar, (seq + q) & 1, off + q * jt, min(jt, nj - q * jt));
+        for (int tl = 0; tl < ntiles; ++tl) {
+            const unsigned sq = seq + tl;
+            const int stg = sq & 1;
+            const bool ok = mbar_wait_bounded(&bar[stg], (sq >> 1) & 1, kWaitLimitNs);
+            if (!__syncthreads_and(ok)) {
+                if (tid == 0) {
+                    for (int u = tl; u < min(tl + 2, ntiles); ++u)
+                        mbar_wait_bounded(&bar[(seq + u) & 1], ((seq + u) >> 1) & 1, kWaitLimitNs);
+                    atomicOr(&a.ctl->err, NB_ERR_TIMEOUT);
+                }
+                return false;
+            }
+            const int len = min(jt, nj - tl * jt);
+            if (MIXED) {
+                const float *s = reinterpret_cast<const float *>(smem) + static_cast<size_t>(stg) * NCF * jt;
+                float2 part[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    part[q] = f2(0.0f);
+                for (int jj = 4 * lj; jj < len; jj += 4 * lanes) {
+                    float2 c0[NCF], c1[NCF];
+#pragma unroll
+                    for (int r = 0; r < NCF; ++r) {
+                        const float4 w = *reinterpret_cast<const float4 *>(s + r * jt + jj);
+                        c0[r] = make_float2(w.x, w.y);
+                        c1[r] = make_float2(w.z, w.w);
+                    }
+                    pair_mixed2(c0, ni, f2(static_cast<float>(a.eps2)), part);
+                    pair_mixed2(c1, ni, f2(static_cast<float>(a.eps2)), part);
+                }
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    two_sum_acc(hi[q], lo[q], __fadd_rn(part[q].x, part[q].y));
+            } else {
+                const double2 *s = reinterpret_cast<const double2 *>(smem) + static_cast<size_t>(stg) * 5 * jt;
+                double part[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    part[q] = 0.0;
+                for (int jj = lj; jj < len; jj += lanes)
+                    pair_fp64(s[jj], s[jt + jj], s[2 * jt + jj], s[3 * jt + jj], s[4 * jt + jj], xi, yi,
+                              zi, vxi, vyi, vzi, axi, ayi, azi, a.eps2, part);
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    acc[q] += part[q];
+            }
+            __syncthreads();
+            if (tid == 0 && tl + 2 < ntiles)
+                issue_ens_tile<MIXED>(a, smem, bar, stg, off + (tl + 2) * jt, min(jt, nj - (tl + 2) * jt));
+        }
+        seq += ntiles;
+        if (MIXED)
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                acc[q] = static_cast<double>(hi[q]) + static_cast<double>(lo[q]);
+        for (int o = lanes >> 1; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        if (valid && lj == 0)
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                a.anew[static_cast<size_t>(q) * P + off + p] = acc[q];
+    }
+    return true;
+}
+
+// Corrector, interpolation and new step for slots [s0, s1) at time tn.
+__device__ void correct_share(const EnsArgs &a, int off, int s0, int s1, double tn)
+{
+    const size_t P = static_cast<size_t>(a.P);
+    for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
+        const int i = a.act[off + k];
+        const double h = tn - a.t[i];
+        const double ih = 1.0 / h;
+        double n2[6] = {0, 0, 0, 0, 0, 0};
+        bool finite = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double *px = a.st + (F_X * 3 + d) * P + i, *pv = a.st + (F_V * 3 + d) * P + i;
+            double *pa = a.st + (F_A * 3 + d) * P + i, *pj = a.st + (F_J * 3 + d) * P + i;
+            double *ps = a.st + (F_S * 3 + d) * P + i, *pc = a.st + (F_C * 3 + d) * P + i;
+            const double a1 = a.anew[(0 + d) * P + off + k];
+            const double j1 = a.anew[(3 + d) * P + off + k];
+            const double s1v = a.anew[(6 + d) * P + off + k];
+            const Corrected r = hermite_correct(h, ih, *px, *pv, *pa, *pj, *ps, a1, j1, s1v);
+            finite = finite && isfinite(r.x1) && isfinite(r.v1) && isfinite(r.c1);
+            *px = r.x1;
+            *pv = r.v1;
+            *pa = a1;
+            *pj = j1;
+            *ps = s1v;
+            *pc = r.c1;
+            n2[0] = fma(a1, a1, n2[0]);
+            n2[1] = fma(j1, j1, n2[1]);
+            n2[2] = fma(s1v, s1v, n2[2]);
+            n2[3] = fma(r.c1, r.c1, n2[3]);
+            n2[4] = fma(r.d1, r.d1, n2[4]);
+            n2[5] = fma(r.e1, r.e1, n2[5]);
+        }
+        a.t[i] = tn;
+        bool hit = false;
+        a.dt[i] = a.dt_shared > 0.0 ? a.dt_shared
+                                    : quantise(aarseth_dt(n2, a.eta), a.dt[i], tn, a.dt_min, a.dt_max, &hit);
+        if (hit)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->floor_hits), 1ull);
+        if (!finite)
+            atomicOr(&a.ctl->err, NB_ERR_NONFINITE);
+    }
+}
+
+// Start-up stores for slots [s0, s1) (all particles, in order).
+__device__ void init_share(const EnsArgs &a, int off, int s0, int s1, int pass)
+{
+    const size_t P = static_cast<size_t>(a.P);
+    for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
+        const int i = off + k;
+        if (pass == 0) {
+            for (int d = 0; d < 3; ++d) {
+                a.st[(F_A * 3 + d) * P + i] = a.anew[(0 + d) * P + i];
+                a.st[(F_J * 3 + d) * P + i] = a.anew[(3 + d) * P + i];
+            }
+            continue;
+        }
+        double na = 0, nj = 0, ns = 0;
+        for (int d = 0; d < 3; ++d) {
+            const double av = a.st[(F_A * 3 + d) * P + i], jv = a.st[(F_J * 3 + d) * P + i];
+            const double sv = a.anew[(6 + d) * P + i];
+            a.st[(F_S * 3 + d) * P + i] = sv;
+            a.st[(F_C * 3 + d) * P + i] = 0.0;
+            na = fma(av, av, na);
+            nj = fma(jv, jv, nj);
+            ns = fma(sv, sv, ns);
+        }
+        bool hit = false;
+        if (a.dt_shared > 0.0) {
+            a.dt[i] = a.dt_shared;
+        } else {
+            na = sqrt(na);
+            a.dt[i] = quantise(a.eta_s * fmin(na / sqrt(nj), sqrt(na / sqrt(ns))), -1.0, 0.0, a.dt_min,
+                               a.dt_max, &hit);
+        }
+        if (hit)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->floor_hits), 1ull);
+    }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ double red_d[32];
+    __shared__ int red_i[32];
+    __shared__ int s_job;
+    __shared__ double s_tmin;
+    __shared__ int s_cnt;
+    __shared__ int s_fail;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = static_cast<int>(cl.block_rank());
+    const int G = static_cast<int>(cl.num_blocks());
+    const int tid = threadIdx.x;
+    unsigned seq = 0;  // TMA stage sequence (continues across chunks and systems)
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        s_fail = 0;
+    }
+    __syncthreads();
+
+    for (;;) {
+        if (rank == 0 && tid == 0)
+            s_job = atomicAdd(a.queue, 1);
+        cl.sync();
+        const int job = *cl.map_shared_rank(&s_job, 0);
+        int fail_any = 0;
+        for (int r = 0; r < G; ++r)
+            fail_any |= *cl.map_shared_rank(&s_fail, r);
+        cl.sync();
+        if (job >= a.nc || fail_any)
+            break;
+        const int c = a.order[job];
+        const int off = a.off[c], n = a.cnt[c];
+        const int nj = MIXED ? (n + 3) / 4 * 4 : n;
+        const int per = (n + G - 1) / G;
+        const int lo = off + min(n, rank * per), hi = off + min(n, (rank + 1) * per);
+
+        if (a.mode == 1) {
+            for (int k = lo - off + tid; k < hi - off; k += blockDim.x)
+                a.act[off + k] = off + k;
+            for (int pass = 0; pass < 2; ++pass) {
+                predict_slice<MIXED>(a, lo, hi, 0.0);
+                cl.sync();
+                const bool ok = eval_share<MIXED>(a, off, nj, lo - off, hi - off, smem, bar, seq);
+                if (!ok && tid == 0)
+                    s_fail = 1;
+                __syncthreads();
+                init_share(a, off, lo - off, hi - off, pass);
+                cl.sync();
+            }
+            continue;
+        }
+
+        int64_t steps = 0;
+        for (;;) {
+            // schedule: next time over the system
+            double mn = INFINITY;
+            for (int i = lo + tid; i < hi; i += blockDim.x)
+                mn = fmin(mn, a.t[i] + a.dt[i]);
+            mn = block_min(mn, red_d);
+            if (tid == 0)
+                s_tmin = mn;
+            cl.sync();
+            double tn = INFINITY;
+            int fail = 0;
+            for (int r = 0; r < G; ++r) {
+                tn = fmin(tn, *cl.map_shared_rank(&s_tmin, r));
+                fail |= *cl.map_shared_rank(&s_fail, r);
+            }
+            if (tn > a.t_end || fail)
+                break;
+            int mine = 0, first = 0, tot = 0;
+            count_due(a, lo, hi, tn, mine, first);
+            const int ex = block_exclusive_scan(mine, red_i, &tot);
+            if (tid == 0)
+                s_cnt = tot;
+            cl.sync();
+            int prefix = 0, total = 0;
+            for (int r = 0; r < G; ++r) {
+                const int v = *cl.map_shared_rank(&s_cnt, r);
+                prefix += r < rank ? v : 0;
+                total += v;
+            }
+            {
+                int pos = prefix + ex;
+                const int per_t = (hi - lo + blockDim.x - 1) / blockDim.x;
+                for (int i = first; i < min(hi, first + per_t); ++i)
+                    if (a.t[i] + a.dt[i] == tn)
+                        a.act[off + pos++] = i;
+            }
+            predict_slice<MIXED>(a, lo, hi, tn);
+            cl.sync();
+            const int q = (total + G - 1) / G;
+            const int s0 = min(total, rank * q), s1 = min(total, s0 + q);
+            const bool ok = eval_share<MIXED>(a, off, nj, s0, s1, smem, bar, seq);
+            if (!ok && tid == 0)
+                s_fail = 1;
+            __syncthreads();
+            if (ok)
+                correct_share(a, off, s0, s1, tn);
+            ++steps;
+            if (rank == 0 && tid == 0)
+                atomicAdd(a.inter, static_cast<unsigned long long>(total) * static_cast<unsigned long long>(n));
+            cl.sync();
+        }
+        if (rank == 0 && tid == 0)
+            a.steps[c] = steps;
+        cl.sync();
+    }
+}
+
+nb_status efail(nb_ensemble *e, nb_status s, const std::string &msg)
+{
+    e->err = msg;
+    return s;
+}
+
+nb_status ecuda(nb_ensemble *e, cudaError_t c, const char *where)
+{
+    e->dead = true;
+    e->err = std::string(where) + ": " + cudaGetErrorString(c);
+    return NB_ECUDA;
+}
+
+#define ECU(e, call)                                \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess)                      \
+            return ecuda((e), e_, #call);           \
+    } while (0)
+
+size_t ens_smem(const nb_ensemble *e)
+{
+    const bool mixed = e->cfg.precision == NB_MIXED;
+    return static_cast<size_t>(2) * (mixed ? NCF * 4 : 5 * 16) * e->jtile;
+}
+
+template <bool MIXED>
+cudaError_t launch_ens(nb_ensemble *e, const EnsArgs &a, int grid_clusters)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid_clusters * e->G);
+    cfg.blockDim = dim3(e->threads);
+    cfg.dynamicSmemBytes = ens_smem(e);
+    cfg.stream = e->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = e->G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ensemble_kernel<MIXED>, a);
+}
+
+template <bool MIXED>
+cudaError_t max_clusters(nb_ensemble *e, int *out)
+{
+    cudaError_t err = cudaFuncSetAttribute(ensemble_kernel<MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(ens_smem(e)));
+    if (err != cudaSuccess)
+        return err;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(e->G);
+    cfg.blockDim = dim3(e->threads);
+    cfg.dynamicSmemBytes = ens_smem(e);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = e->G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(out, ensemble_kernel<MIXED>, &cfg);
+}
+
+EnsArgs make_args(nb_ensemble *e, int mode, double t_end)
+{
+    EnsArgs a;
+    a.nc = e->nc;
+    a.off = e->d_off;
+    a.cnt = e->d_cnt;
+    a.order = e->d_order;
+    a.P = static_cast<int>(e->P);
+    a.st = e->st;
+    a.t = e->t;
+    a.dt = e->dt;
+    a.m = e->m;
+    a.jb64 = e->jb64;
+    a.jf32 = e->jf32;
+    a.act = e->act;
+    a.anew = e->anew;
+    a.queue = e->queue;
+    a.steps = e->steps;
+    a.inter = e->inter;
+    a.ctl = e->ctl;
+    a.t_end = t_end;
+    a.eps2 = e->eps * e->eps;
+    a.eta = e->cfg.eta;
+    a.eta_s = e->cfg.eta_s;
+    a.dt_min = e->cfg.dt_min;
+    a.dt_max = e->cfg.dt_max;
+    a.dt_shared = e->cfg.dt_shared;
+    a.mode = mode;
+    a.jtile = e->jtile;
+    return a;
+}
+
+// Enqueue one persistent launch (queue reset + kernel) on e->stream.
+nb_status enqueue_run(nb_ensemble *e, int mode, double t_end)
+{
+    const bool mixed = e->cfg.precision == NB_MIXED;
+    int maxc = 0;
+    ECU(e, mixed ? max_clusters<true>(e, &maxc) : max_clusters<false>(e, &maxc));
+    if (maxc < 1)
+        return efail(e, NB_EINVAL, "ensemble launch shape does not fit on an SM");
+    const int grid = std::min(maxc, e->nc);
+    ECU(e, cudaMemsetAsync(e->queue, 0, sizeof(int), e->stream));
+    const EnsArgs a = make_args(e, mode, t_end);
+    ECU(e, mixed ? launch_ens<true>(e, a, grid) : launch_ens<false>(e, a, grid));
+    return NB_OK;
+}
+
+nb_status ens_sync(nb_ensemble *e)
+{
+    ECU(e, cudaMemcpyAsync(e->ctl_h, e->ctl, sizeof(nb_ctl), cudaMemcpyDeviceToHost, e->stream));
+    ECU(e, cudaStreamSynchronize(e->stream));
+    if (e->ctl_h->err) {
+        const int err = e->ctl_h->err;
+        ECU(e, cudaMemsetAsync(&e->ctl->err, 0, sizeof(int32_t), e->stream));
+        ECU(e, cudaStreamSynchronize(e->stream));
+        if (err & NB_ERR_TIMEOUT)
+            return efail(e, NB_ETIMEOUT, "a device-side wait timed out in the ensemble launch");
+        return efail(e, NB_ENONFINITE, "non-finite value produced on the device");
+    }
+    return NB_OK;
+}
+
+void ens_free_all(nb_ensemble *e)
+{
+    if (e->exec)
+        cudaGraphExecDestroy(e->exec);
+    if (e->graph)
+        cudaGraphDestroy(e->graph);
+    cudaFree(e->d_off);
+    cudaFree(e->d_cnt);
+    cudaFree(e->d_order);
+    cudaFree(e->m);
+    cudaFree(e->st);
+    cudaFree(e->t);
+    cudaFree(e->dt);
+    cudaFree(e->anew);
+    cudaFree(e->jb64);
+    cudaFree(e->jf32);
+    cudaFree(e->act);
+    cudaFree(e->queue);
+    cudaFree(e->steps);
+    cudaFree(e->inter);
+    cudaFree(e->ctl);
+    if (e->ctl_h)
+        cudaFreeHost(e->ctl_h);
+    if (e->own_stream && e->stream)
+        cudaStreamDestroy(e->stream);
+}
+
+bool pow2(double x)
+{
+    int ex;
+    return x > 0 && std::isfinite(x) && std::frexp(x, &ex) == 0.5;
+}
+
+}  // namespace
+
+extern "C" {
+
+nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *sizes, const double *m,
+                           const double *x, const double *v, double eps, const nb_config *cfg)
+{
+    if (!out) {
+        nb_set_thread_error("out must not be NULL");
+        return NB_EINVAL;
+    }
+    *out = nullptr;
+    nb_config cf;
+    if (cfg)
+        cf = *cfg;
+    else
+        nb_config_default(&cf);
+    if (n_systems < 1 || !sizes || !m || !x || !v) {
+        nb_set_thread_error("n_systems >= 1 and non-NULL sizes, m, x, v are required");
+        return NB_EINVAL;
+    }
+    if ((cf.precision != NB_FP64 && cf.precision != NB_MIXED) || !(cf.eta > 0) || !(cf.eta_s > 0) ||
+        !pow2(cf.dt_min) || !pow2(cf.dt_max) || cf.dt_min > cf.dt_max ||
+        (cf.dt_shared != 0.0 && !pow2(cf.dt_shared))) {
+        nb_set_thread_error("invalid configuration");
+        return NB_EINVAL;
+    }
+    const double eps_min = cf.precision == NB_MIXED ? std::ldexp(1.0, -40) : std::ldexp(1.0, -60);
+    if (!(eps >= eps_min) || !(eps <= 1e18)) {
+        nb_set_thread_error("eps out of range");
+        return NB_EINVAL;
+    }
+    int64_t total = 0, padded = 0;
+    for (int c = 0; c < n_systems; ++c) {
+        if (sizes[c] < 1) {
+            nb_set_thread_error("every system needs at least one particle");
+            return NB_EINVAL;
+        }
+        total += sizes[c];
+        padded += (sizes[c] + 3) / 4 * 4;
+    }
+    if (padded > 0x7fffffffLL / 16) {
+        nb_set_thread_error("ensemble too large");
+        return NB_EINVAL;
+    }
+    for (int64_t i = 0; i < total; ++i)
+        if (!std::isfinite(m[i]) || m[i] < 0.0) {
+            nb_set_thread_error("masses must be finite and >= 0");
+            return NB_ENONFINITE;
+        }
+    for (int64_t i = 0; i < 3 * total; ++i)
+        if (!std::isfinite(x[i]) || !std::isfinite(v[i])) {
+            nb_set_thread_error("positions and velocities must be finite");
+            return NB_ENONFINITE;
+        }
+
+    nb_ensemble *e = new nb_ensemble();
+    e->cfg = cf;
+    e->eps = eps;
+    e->nc = n_systems;
+    e->P = padded;
+    e->jtile = cf.precision == NB_MIXED ? 256 : 128;
+    auto bail = [&](nb_status s) {
+        nb_set_thread_error(e->err.c_str());
+        ens_free_all(e);
+        delete e;
+        return s;
+    };
+#define EI(call)                                              \
+    do {                                                      \
+        cudaError_t c_ = (call);                              \
+        if (c_ != cudaSuccess) {                              \
+            ecuda(e, c_, #call);                              \
+            return bail(c_ == cudaErrorMemoryAllocation ? NB_ENOMEM : NB_ECUDA); \
+        }                                                     \
+    } while (0)
+    EI(cudaGetDevice(&e->dev));
+    if (cf.stream) {
+        e->stream = static_cast<cudaStream_t>(cf.stream);
+    } else {
+        EI(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
+        e->own_stream = true;
+    }
+    e->off.resize(n_systems);
+    e->cnt.resize(n_systems);
+    {
+        int64_t o = 0;
+        for (int c = 0; c < n_systems; ++c) {
+            e->off[c] = static_cast<int32_t>(o);
+            e->cnt[c] = static_cast<int32_t>(sizes[c]);
+            o += (sizes[c] + 3) / 4 * 4;
+        }
+    }
+    std::vector<int32_t> order(n_systems);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return e->cnt[a] > e->cnt[b]; });
+    const size_t P = static_cast<size_t>(e->P);
+    EI(cudaMalloc(&e->d_off, n_systems * sizeof(int32_t)));
+    EI(cudaMalloc(&e->d_cnt, n_systems * sizeof(int32_t)));
+    EI(cudaMalloc(&e->d_order, n_systems * sizeof(int32_t)));
+    EI(cudaMalloc(&e->m, P * sizeof(double)));
+    EI(cudaMalloc(&e->st, 18 * P * sizeof(double)));
+    EI(cudaMalloc(&e->t, P * sizeof(double)));
+    EI(cudaMalloc(&e->dt, P * sizeof(double)));
+    EI(cudaMalloc(&e->anew, 9 * P * sizeof(double)));
+    EI(cudaMalloc(&e->act, P * sizeof(int32_t)));
+    if (cf.precision == NB_MIXED) {
+        EI(cudaMalloc(&e->jf32, 13 * P * sizeof(float)));
+        EI(cudaMemsetAsync(e->jf32, 0, 13 * P * sizeof(float), e->stream));
+    } else {
+        EI(cudaMalloc(&e->jb64, 5 * P * sizeof(double2)));
+        EI(cudaMemsetAsync(e->jb64, 0, 5 * P * sizeof(double2), e->stream));
+    }
+    EI(cudaMalloc(&e->queue, sizeof(int)));
+    EI(cudaMalloc(&e->steps, n_systems * sizeof(int64_t)));
+    EI(cudaMalloc(&e->inter, sizeof(unsigned long long)));
+    EI(cudaMalloc(&e->ctl, sizeof(nb_ctl)));
+    EI(cudaMallocHost(&e->ctl_h, sizeof(nb_ctl)));
+    std::vector<double> hst(18 * P, 0.0), hm(P, 0.0), ht(P, 0.0);
+    {
+        int64_t src = 0;
+        for (int c = 0; c < n_systems; ++c)
+            for (int k = 0; k < e->cnt[c]; ++k, ++src) {
+                const size_t i = static_cast<size_t>(e->off[c]) + k;
+                hm[i] = m[src];
+                for (int d = 0; d < 3; ++d) {
+                    hst[(F_X * 3 + d) * P + i] = x[3 * src + d];
+                    hst[(F_V * 3 + d) * P + i] = v[3 * src + d];
+                }
+            }
+    }
+    EI(cudaMemcpyAsync(e->d_off, e->off.data(), n_systems * sizeof(int32_t), cudaMemcpyHostToDevice, e->stream));
+    EI(cudaMemcpyAsync(e->d_cnt, e->cnt.data(), n_systems * sizeof(int32_t), cudaMemcpyHostToDevice, e->stream));
+    EI(cudaMemcpyAsync(e->d_order, order.data(), n_systems * sizeof(int32_t), cudaMemcpyHostToDevice, e->stream));
+    EI(cudaMemcpyAsync(e->st, hst.data(), 18 * P * sizeof(double), cudaMemcpyHostToDevice, e->stream));
+    EI(cudaMemcpyAsync(e->m, hm.data(), P * sizeof(double), cudaMemcpyHostToDevice, e->stream));
+    EI(cudaMemcpyAsync(e->t, ht.data(), P * sizeof(double), cudaMemcpyHostToDevice, e->stream));
+    // padding particles: dt = +inf keeps them out of every schedule
+    std::vector<double> hdt(P, INFINITY);
+    EI(cudaMemcpyAsync(e->dt, hdt.data(), P * sizeof(double), cudaMemcpyHostToDevice, e->stream));
+    EI(cudaMemsetAsync(e->steps, 0, n_systems * sizeof(int64_t), e->stream));
+    EI(cudaMemsetAsync(e->inter, 0, sizeof(unsigned long long), e->stream));
+    EI(cudaMemsetAsync(e->ctl, 0, sizeof(nb_ctl), e->stream));
+    nb_status s = enqueue_run(e, 1, 0.0);
+    if (s != NB_OK)
+        return bail(s);
+    e->launches += 1;
+    s = ens_sync(e);
+    if (s != NB_OK)
+        return bail(s);
+    *out = e;
+    return NB_OK;
+#undef EI
+}
+
+nb_status nb_ensemble_set_shape(nb_ensemble *e, int32_t ctas_per_system, int32_t threads, int32_t jtile)
+{
+    if (!e)
+        return NB_EINVAL;
+    if (e->dead)
+        return NB_ECUDA;
+    if (ctas_per_system < 1 || ctas_per_system > 8 || threads < 64 || threads > kEnsThreads ||
+        threads % 32 || jtile < 4 || jtile > 1024 || jtile % 4)
+        return efail(e, NB_EINVAL, "ctas_per_system in [1, 8], threads a multiple of 32 in [64, 256], "
+                                   "jtile a multiple of 4 in [4, 1024]");
+    e->G = ctas_per_system;
+    e->threads = threads;
+    e->jtile = jtile;
+    if (e->exec) {
+        cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
+    }
+    if (e->graph) {
+        cudaGraphDestroy(e->graph);
+        e->graph = nullptr;
+    }
+    e->graph_t_end = -1.0;
+    return NB_OK;
+}
+
+nb_status nb_ensemble_run(nb_ensemble *e, double t_end, int use_graph)
+{
+    if (!e)
+        return NB_EINVAL;
+    if (e->dead)
+        return NB_ECUDA;
+    const double unit = e->cfg.dt_shared > 0.0 ? e->cfg.dt_shared : e->cfg.dt_max;
+    if (!std::isfinite(t_end) || t_end < 0.0 || std::fmod(t_end, unit) != 0.0)
+        return efail(e, NB_EINVAL, "t_end must be a non-negative multiple of dt_max (dt_shared)");
+    if (!use_graph) {
+        nb_status s = enqueue_run(e, 0, t_end);
+        if (s != NB_OK)
+            return s;
+        e->launches += 1;
+        return ens_sync(e);
+    }
+    if (!e->exec || e->graph_t_end != t_end) {
+        if (e->exec) {
+            cudaGraphExecDestroy(e->exec);
+            e->exec = nullptr;
+        }
+        if (e->graph) {
+            cudaGraphDestroy(e->graph);
+            e->graph = nullptr;
+        }
+        // occupancy query and attributes before capture
+        int maxc = 0;
+        ECU(e, e->cfg.precision == NB_MIXED ? max_clusters<true>(e, &maxc) : max_clusters<false>(e, &maxc));
+        ECU(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+        nb_status s = enqueue_run(e, 0, t_end);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+        if (s != NB_OK) {
+            if (g)
+                cudaGraphDestroy(g);
+            return s;
+        }
+        ECU(e, ce);
+        e->graph = g;
+        ECU(e, cudaGraphInstantiate(&e->exec, e->graph, 0));
+        e->graph_t_end = t_end;
+    }
+    ECU(e, cudaGraphLaunch(e->exec, e->stream));
+    e->launches += 1;
+    return ens_sync(e);
+}
+
+nb_status nb_ensemble_get_state(nb_ensemble *e, double *x, double *v, double *a, double *j, double *s,
+                                double *c, double *t, double *dt)
+{
+    if (!e)
+        return NB_EINVAL;
+    if (e->dead)
+        return NB_ECUDA;
+    const size_t P = static_cast<size_t>(e->P);
+    std::vector<double> hst(18 * P), ht(P), hdt(P);
+    ECU(e, cudaMemcpyAsync(hst.data(), e->st, 18 * P * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
+    ECU(e, cudaMemcpyAsync(ht.data(), e->t, P * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
+    ECU(e, cudaMemcpyAsync(hdt.data(), e->dt, P * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
+    nb_status st = ens_sync(e);
+    if (st != NB_OK)
+        return st;
+    double *outs[6] = {x, v, a, j, s, c};
+    int64_t dst = 0;
+    for (int q = 0; q < e->nc; ++q)
+        for (int k = 0; k < e->cnt[q]; ++k, ++dst) {
+            const size_t i = static_cast<size_t>(e->off[q]) + k;
+            for (int f = 0; f < 6; ++f)
+                if (outs[f])
+                    for (int d = 0; d < 3; ++d)
+                        outs[f][3 * dst + d] = hst[(f * 3 + d) * P + i];
+            if (t)
+                t[dst] = ht[i];
+            if (dt)
+                dt[dst] = hdt[i];
+        }
+    return NB_OK;
+}
+
+nb_status nb_ensemble_stats(nb_ensemble *e, int64_t *steps, double *interactions, int64_t *launches)
+{
+    if (!e)
+        return NB_EINVAL;
+    if (e->dead)
+        return NB_ECUDA;
+    unsigned long long it = 0;
+    if (steps)
+        ECU(e, cudaMemcpyAsync(steps, e->steps, e->nc * sizeof(int64_t), cudaMemcpyDeviceToHost, e->stream));
+    ECU(e, cudaMemcpyAsync(&it, e->inter, sizeof(it), cudaMemcpyDeviceToHost, e->stream));
+    ECU(e, cudaStreamSynchronize(e->stream));
+    if (interactions)
+        *interactions = static_cast<double>(it);
+    if (launches)
+        *launches = e->launches;
+    return NB_OK;
+}
+
+const char *nb_ensemble_last_error(const nb_ensemble *e)
+{
+    return e ? e->err.c_str() : nb_last_error(nullptr);
+}
+
+void nb_ensemble_free(nb_ensemble *e)
+{
+    if (!e)
+        return;
+    cudaStreamSynchronize(e->stream);
+    ens_free_all(e);
+    delete e;
+}
+
+}  // extern "C"

@@ -18,9 +18,12 @@
 #include <algorithm>
 #include <mutex>
 
+#include "nb_device.cuh"
 #include "nb_internal.cuh"
 
 namespace {
+
+using namespace nbk;
 
 // Largest block for KI i-particles per thread (register budget: 255 per
 // thread at 256 threads, 128 at 512).
@@ -111,47 +114,6 @@ __device__ __forceinline__ void store_or_fold(const EvalArgs &a, double (&acc)[9
 }
 
 // ------------------------------------------------------------------ FP64
-
-// One softened pair term in FP64, accumulated into p[0..8]
-// (acc, jerk, snap).  With r, v, a the differences j - i, R = r.r + eps^2,
-// q = R^(-1/2), mu = m_j q^3, alpha = (r.v) q^2, beta = (v.v + r.a) q^2 +
-// alpha^2, u = v - 3 alpha r and w = a - 6 alpha u - 3 beta r:
-//   acc += mu r,  jerk += mu u,  snap += mu w.
-// (jerk = mu v - 3 alpha A and snap = mu a - 6 alpha J - 3 beta A rewritten
-// so that every step is one fused multiply-add.)
-__device__ __forceinline__ void pair_fp64(const double2 &p0, const double2 &p1, const double2 &p2,
-                                          const double2 &p3, const double2 &p4, double xi,
-                                          double yi, double zi, double vxi, double vyi, double vzi,
-                                          double axi, double ayi, double azi, double eps2,
-                                          double *p)
-{
-    const double dx = p0.x - xi, dy = p0.y - yi, dz = p1.x - zi;
-    const double mj = p1.y;
-    const double dvx = p2.x - vxi, dvy = p2.y - vyi, dvz = p3.x - vzi;
-    const double dax = p3.y - axi, day = p4.x - ayi, daz = p4.y - azi;
-    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
-    const double rv = fma(dx, dvx, fma(dy, dvy, dz * dvz));
-    const double sv = fma(dx, dax, fma(dy, day, fma(dz, daz, fma(dvx, dvx, fma(dvy, dvy, dvz * dvz)))));
-    const double q = nbk::rsqrt_fp64(r2);
-    const double q2 = q * q;
-    const double mu = mj * q * q2;
-    const double al = rv * q2;
-    const double be = fma(al, al, sv * q2);
-    const double a3 = 3.0 * al, a6 = 6.0 * al, b3 = 3.0 * be;
-    const double ux = fma(-a3, dx, dvx), uy = fma(-a3, dy, dvy), uz = fma(-a3, dz, dvz);
-    const double wx = fma(-a6, ux, fma(-b3, dx, dax));
-    const double wy = fma(-a6, uy, fma(-b3, dy, day));
-    const double wz = fma(-a6, uz, fma(-b3, dz, daz));
-    p[0] = fma(mu, dx, p[0]);
-    p[1] = fma(mu, dy, p[1]);
-    p[2] = fma(mu, dz, p[2]);
-    p[3] = fma(mu, ux, p[3]);
-    p[4] = fma(mu, uy, p[4]);
-    p[5] = fma(mu, uz, p[5]);
-    p[6] = fma(mu, wx, p[6]);
-    p[7] = fma(mu, wy, p[7]);
-    p[8] = fma(mu, wz, p[8]);
-}
 
 template <int KI>
 __global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs a)
@@ -267,66 +229,6 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs
 // moves their cost off the FMA pipe).  Each thread sums a tile in
 // FP32 (two halves), then folds the tile sum into a TwoSum-compensated
 // (hi, lo) accumulator.
-
-constexpr int NCF = 13;  // FP32 rows of the mixed j-buffer
-
-__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-__device__ __forceinline__ float rsqrt_est(float x)
-{
-    float y;
-    asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float rcp_est(float x)
-{
-    float y;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Two pair terms (j, j+1) for one i.  c[] are the 13 j-rows (as pairs), ni[]
-// the negated i-values (-xh,-yh,-zh,-xl,-yl,-zl,-vx,-vy,-vz,-ax,-ay,-az).
-// With r, v, a = j - i, R = r.r + eps^2, q = R^(-1/2), mu = m_j q^3,
-// alpha = (r.v) q^2, beta = (v.v + r.a) q^2 + alpha^2, u = v - 3 alpha r and
-// w = a - 6 alpha u - 3 beta r:  acc += mu r, jerk += mu u, snap += mu w.
-__device__ __forceinline__ void pair_mixed2(const float2 (&c)[NCF], const float2 (&ni)[12],
-                                            float2 eps2, float2 (&p)[9])
-{
-    const float2 dx = add2(add2(c[0], ni[0]), add2(c[4], ni[3]));
-    const float2 dy = add2(add2(c[1], ni[1]), add2(c[5], ni[4]));
-    const float2 dz = add2(add2(c[2], ni[2]), add2(c[6], ni[5]));
-    const float2 dvx = add2(c[7], ni[6]), dvy = add2(c[8], ni[7]), dvz = add2(c[9], ni[8]);
-    const float2 dax = add2(c[10], ni[9]), day = add2(c[11], ni[10]), daz = add2(c[12], ni[11]);
-    const float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
-    const float2 rv = fma2(dx, dvx, fma2(dy, dvy, mul2(dz, dvz)));
-    const float2 sv = fma2(dx, dax, fma2(dy, day, fma2(dz, daz, fma2(dvx, dvx, fma2(dvy, dvy, mul2(dvz, dvz))))));
-    // q = R^(-1/2) and q^2 = 1/R both from the special-function unit, so the
-    // squaring error of an estimate does not enter mu = m q^3 and alpha/beta
-    const float2 q = make_float2(rsqrt_est(r2.x), rsqrt_est(r2.y));
-    const float2 q2 = make_float2(rcp_est(r2.x), rcp_est(r2.y));
-    const float2 mu = mul2(mul2(c[3], q), q2);
-    const float2 al = mul2(rv, q2);
-    const float2 be = fma2(al, al, mul2(sv, q2));
-    const float2 na3 = mul2(al, f2(-3.0f)), na6 = mul2(al, f2(-6.0f)), nb3 = mul2(be, f2(-3.0f));
-    const float2 ux = fma2(na3, dx, dvx), uy = fma2(na3, dy, dvy), uz = fma2(na3, dz, dvz);
-    const float2 wx = fma2(na6, ux, fma2(nb3, dx, dax));
-    const float2 wy = fma2(na6, uy, fma2(nb3, dy, day));
-    const float2 wz = fma2(na6, uz, fma2(nb3, dz, daz));
-    p[0] = fma2(mu, dx, p[0]);
-    p[1] = fma2(mu, dy, p[1]);
-    p[2] = fma2(mu, dz, p[2]);
-    p[3] = fma2(mu, ux, p[3]);
-    p[4] = fma2(mu, uy, p[4]);
-    p[5] = fma2(mu, uz, p[5]);
-    p[6] = fma2(mu, wx, p[6]);
-    p[7] = fma2(mu, wy, p[7]);
-    p[8] = fma2(mu, wz, p[8]);
-}
 
 // 13 bulk copies per tile, one per FP32 row; len and j0 are multiples of 4.
 __device__ __forceinline__ void issue_tile_rows(unsigned char *smem, uint64_t *bar, const EvalArgs &a,

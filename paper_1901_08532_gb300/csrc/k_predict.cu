@@ -3,26 +3,13 @@
 // common time t through crackle, in FP64, and written into the layout the
 // evaluation kernel streams (one coalesced pass): FP64 records, or for the
 // mixed path 13 FP32 rows with positions split into hi + lo.
+#include "nb_device.cuh"
 #include "nb_internal.cuh"
 
 namespace {
 
-struct Taylor {
-    double x, v, a;
-};
-
-// Horner form of x + v d + a d^2/2 + j d^3/6 + s d^4/24 + c d^5/120 and its
-// first two derivatives.
-__device__ __forceinline__ Taylor taylor(double x, double v, double a, double j, double s, double c,
-                                         double d)
-{
-    const double d2 = 0.5 * d, d3 = d * (1.0 / 3.0), d4 = 0.25 * d, d5 = 0.2 * d;
-    Taylor r;
-    r.x = fma(d, fma(d2, fma(d3, fma(d4, fma(d5, c, s), j), a), v), x);
-    r.v = fma(d, fma(d2, fma(d3, fma(d4, c, s), j), a), v);
-    r.a = fma(d, fma(d2, fma(d3, c, s), j), a);
-    return r;
-}
+using nbk::Taylor;
+using nbk::taylor;
 
 __global__ void __launch_bounds__(256) predict_kernel(const double *__restrict__ st,
                                                       const double *__restrict__ ti,

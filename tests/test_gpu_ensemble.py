@@ -1,0 +1,106 @@
+"""Ensembles of independent systems in one persistent launch, against the
+FP64 oracle run system by system."""
+import numpy as np
+import pytest
+
+import nb_inputs as ni
+import oracle as O
+from nbhelp import nb_gpu, rel_err
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [2, 5, 33, 300, 1000, 64, 257]
+
+
+def _systems(sizes, base_seed=40):
+    ms, xs, vs = [], [], []
+    for k, n in enumerate(sizes):
+        m, x, v = ni.plummer(n, base_seed + k)
+        ms.append(m)
+        xs.append(x)
+        vs.append(v)
+    return ms, xs, vs
+
+
+def _concat(ms, xs, vs):
+    return np.concatenate(ms), np.concatenate(xs), np.concatenate(vs)
+
+
+def test_fp64_ensemble_matches_oracle_per_system():
+    nb = nb_gpu()
+    ms, xs, vs = _systems(SIZES)
+    eps, t_end = 1e-4, 0.125
+    ens = nb.Ensemble(SIZES, *_concat(ms, xs, vs), eps)
+    ens.run(t_end)
+    st = ens.state()
+    steps, inter, _ = ens.stats()
+    ens.close()
+    o = 0
+    for k, n in enumerate(SIZES):
+        ref = O.System(ms[k], xs[k], vs[k], eps)
+        nsteps, _ = ref.run_until(t_end)
+        sr = ref.state()
+        assert steps[k] == nsteps, (k, steps[k], nsteps)
+        for f in ("x", "v"):
+            assert rel_err(st[f][o:o + n], sr[f]).max() < 1e-10, (k, f)
+        np.testing.assert_array_equal(st["t"][o:o + n], sr["t"])
+        np.testing.assert_array_equal(st["dt"][o:o + n], sr["dt"])
+        o += n
+    assert inter > 0
+
+
+def test_fp64_ensemble_launch_shapes_agree():
+    nb = nb_gpu()
+    ms, xs, vs = _systems(SIZES, 60)
+    out = []
+    for g, thr in ((1, 256), (4, 128), (8, 256)):
+        ens = nb.Ensemble(SIZES, *_concat(ms, xs, vs), 1e-4, dt_max=2.0 ** -5)
+        ens.set_shape(g, thr)
+        ens.run(2.0 ** -5, use_graph=(g != 4))
+        out.append(ens.state())
+        ens.close()
+    for st in out[1:]:
+        for f in ("x", "v", "a"):
+            assert rel_err(st[f], out[0][f]).max() < 1e-12, f
+        np.testing.assert_array_equal(st["t"], out[0]["t"])
+
+
+def test_mixed_ensemble_tracks_fp64_and_conserves_energy():
+    nb = nb_gpu()
+    sizes = [300, 1000, 64]
+    ms, xs, vs = _systems(sizes, 80)
+    eps, t_end = 1e-4, 0.125
+    res = {}
+    for prec in (nb.NB_FP64, nb.NB_MIXED):
+        ens = nb.Ensemble(sizes, *_concat(ms, xs, vs), eps, precision=prec)
+        ens.run(t_end)
+        res[prec] = ens.state()
+        ens.close()
+    o = 0
+    for k, n in enumerate(sizes):
+        e0 = sum(O.energy(ms[k], xs[k], vs[k], eps))
+        for prec in (nb.NB_FP64, nb.NB_MIXED):
+            st = res[prec]
+            e1 = sum(O.energy(ms[k], st["x"][o:o + n], st["v"][o:o + n], eps))
+            assert abs((e1 - e0) / e0) < 1e-8, (k, prec)
+        assert rel_err(res[nb.NB_MIXED]["x"][o:o + n], res[nb.NB_FP64]["x"][o:o + n]).max() < 1e-6
+        o += n
+
+
+def test_graph_replay_continues_the_integration():
+    nb = nb_gpu()
+    sizes = [33, 300]
+    ms, xs, vs = _systems(sizes, 90)
+    eps = 1e-4
+    a = nb.Ensemble(sizes, *_concat(ms, xs, vs), eps)
+    a.run(0.125)
+    a.run(0.25)
+    _, _, launches = a.stats()
+    b = nb.Ensemble(sizes, *_concat(ms, xs, vs), eps)
+    b.run(0.25, use_graph=False)
+    sa, sb = a.state(), b.state()
+    a.close()
+    b.close()
+    for f in ("x", "v", "a", "j", "s", "t", "dt"):
+        np.testing.assert_array_equal(sa[f], sb[f])
+    assert launches == 3  # start-up + two graph launches

@@ -68,8 +68,18 @@ def parse():
                    help="only launch the evaluation kernel --reps times on --n particles with "
                         "--n-act active (a small case for ncu captures)")
     p.add_argument("--n-act", type=int, default=4096)
-    p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "both"])
     p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--ensemble", action="store_true",
+                   help="ensemble workload: 256 Plummer systems, N log-uniform in [256, 16384] "
+                        "(seed 4), each to --ens-t-end; one persistent launch vs one at a time")
+    p.add_argument("--ens-t-end", type=float, default=0.25)
+    p.add_argument("--ens-systems", type=int, default=256)
+    p.add_argument("--ens-shapes", default="8x256",
+                   help="comma-separated ctas_per_system x threads shapes to time")
+    p.add_argument("--ens-sample", type=int, default=8,
+                   help="systems in the one-at-a-time comparison (0: skip)")
+    p.add_argument("--ens-cmp-t-end", type=float, default=0.125)
     return p.parse_args()
 
 
@@ -459,12 +469,90 @@ def profile_eval(args):
     return 0
 
 
+def ensemble_bench(args):
+    """Batched ensemble (256 Plummer systems, N log-uniform in [256, 16384],
+    seed 4, eps = 1e-4, own block steps): (1) all systems in one persistent,
+    graph-captured launch to --ens-t-end; (2) the batching gain on a sample
+    of --ens-sample systems spread over the size range, each advanced one at
+    a time through nb_run_until, against the same sample as one ensemble, to
+    --ens-cmp-t-end.  Interactions per second of each."""
+    import numpy as np
+    import torch
+
+    import nb_inputs as ni
+    import paper_1901_08532_gb300 as nb
+    torch.cuda.set_device(0)
+    sizes = ni.ensemble_sizes(args.ens_systems, 4)
+    parts = [ni.plummer(int(n), 1000 + k) for k, n in enumerate(sizes)]
+
+    def cat(idx):
+        return (np.concatenate([parts[k][0] for k in idx]), np.concatenate([parts[k][1] for k in idx]),
+                np.concatenate([parts[k][2] for k in idx]))
+
+    def run_ens(idx, prec, shape, t_end):
+        g, thr = shape
+        ens = nb.Ensemble(sizes[idx], *cat(idx), EPS, precision=prec)
+        ens.set_shape(g, thr)
+        _, it0, _ = ens.stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ens.run(t_end)
+        el = time.perf_counter() - t0
+        steps, it1, launches = ens.stats()
+        ens.close()
+        return {"seconds": el, "interactions": it1 - it0, "interactions_per_s": (it1 - it0) / el,
+                "block_steps": int(steps.sum()), "max_steps": int(steps.max())}
+
+    out = {"workload": f"ensemble_{args.ens_systems}_plummer_N256-16384_eps1e-4",
+           "systems": int(sizes.size), "particles": int(sizes.sum())}
+    precs = ("mixed", "fp64") if args.prec == "both" else (args.prec,)
+    shapes = [tuple(int(q) for q in sh.split("x")) for sh in args.ens_shapes.split(",")]
+    everyone = list(range(sizes.size))
+    for prec_name in precs:
+        prec = nb.NB_MIXED if prec_name == "mixed" else nb.NB_FP64
+        res = {"t_end": args.ens_t_end, "shapes": {}}
+        for sh in shapes:
+            r = run_ens(everyone, prec, sh, args.ens_t_end)
+            res["shapes"]["%dx%d" % sh] = r
+            print(json.dumps({"progress": prec_name, "shape": sh, **r}), flush=True)
+        best_shape = max(res["shapes"], key=lambda k: res["shapes"][k]["interactions_per_s"])
+        res["best_shape"] = best_shape
+        res["interactions_per_s"] = res["shapes"][best_shape]["interactions_per_s"]
+        if args.ens_sample > 0:
+            order = np.argsort(sizes)
+            idx = [int(order[q]) for q in np.linspace(0, sizes.size - 1, args.ens_sample).astype(int)]
+            sh = tuple(int(q) for q in best_shape.split("x"))
+            batched = run_ens(idx, prec, sh, args.ens_cmp_t_end)
+            tot_el, tot_it = 0.0, 0.0
+            for k in idx:
+                ctx = nb.NBody(*parts[k], EPS, precision=prec)
+                _, i0 = ctx.counters()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ctx.run_until(args.ens_cmp_t_end)
+                tot_el += time.perf_counter() - t0
+                _, i1 = ctx.counters()
+                tot_it += i1 - i0
+                ctx.close()
+            res["sample"] = {"systems": idx, "sizes": [int(sizes[k]) for k in idx],
+                             "t_end": args.ens_cmp_t_end, "ensemble": batched,
+                             "one_at_a_time": {"seconds": tot_el, "interactions": tot_it,
+                                               "interactions_per_s": tot_it / tot_el},
+                             "speedup": batched["interactions_per_s"] / (tot_it / tot_el)}
+            print(json.dumps({"progress": prec_name, "sample": res["sample"]}), flush=True)
+        out[prec_name] = res
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_eval:
         return profile_eval(args)
+    if args.ensemble:
+        return ensemble_bench(args)
     return run_ours(args)
 
 

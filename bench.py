@@ -80,6 +80,10 @@ def parse():
     p.add_argument("--ens-sample", type=int, default=8,
                    help="systems in the one-at-a-time comparison (0: skip)")
     p.add_argument("--ens-cmp-t-end", type=float, default=0.125)
+    p.add_argument("--adjoint", action="store_true",
+                   help="differentiable fixed-step trajectory: Plummer N=--n (default 8192 in this "
+                        "mode), eps 1e-3, dt 2^-10, 64 steps, checkpoints every 8; forward and "
+                        "backward times")
     return p.parse_args()
 
 
@@ -545,8 +549,45 @@ def ensemble_bench(args):
     return 0
 
 
+def adjoint_bench(args):
+    """Config: Plummer N = 8192, eps = 1e-3, shared step 2^-10, 64 steps,
+    loss = sum m |x(T)|^2, gradients with respect to x0, v0, m through the
+    hand-written adjoint kernel with checkpoints every 8 steps."""
+    import numpy as np
+    import torch
+
+    import nb_inputs as ni
+    from paper_1901_08532_gb300 import adjoint as A
+    torch.cuda.set_device(0)
+    n = args.n if args.n != N_BODY else 8192
+    eps, h, steps = 1e-3, 2.0 ** -10, 64
+    m, x, v = ni.plummer(n, 5)
+    mt, xt, vt = (torch.tensor(q, dtype=torch.float64, device="cuda") for q in (m, x, v))
+    with torch.no_grad():
+        A.trajectory(mt, xt, vt, eps, h, 2, 0)          # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.no_grad():
+        A.trajectory(mt, xt, vt, eps, h, steps, 0)
+    torch.cuda.synchronize()
+    fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L, gx, gv, gm = A.loss_and_grads(mt, xt, vt, eps, h, steps, checkpoint_every=8)
+    torch.cuda.synchronize()
+    both = time.perf_counter() - t0
+    inter_fwd = float(n) * n * (steps + 2)
+    print(json.dumps({"workload": f"adjoint_plummer_N{n}_eps1e-3_dt2^-10_64steps_ckpt8",
+                      "forward_s": fwd, "forward_interactions_per_s": inter_fwd / fwd,
+                      "forward_plus_backward_s": both, "backward_s": both - fwd,
+                      "backward_over_forward": (both - fwd) / fwd,
+                      "loss": float(L), "grad_norms": [float(g.norm()) for g in (gx, gv, gm)]}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.adjoint:
+        return adjoint_bench(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_eval:

@@ -36,6 +36,7 @@
 #ifndef NB_H
 #define NB_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -239,6 +240,34 @@ nb_status nb_ensemble_stats(nb_ensemble *e, int64_t *steps, double *interactions
 const char *nb_ensemble_last_error(const nb_ensemble *e);
 
 void nb_ensemble_free(nb_ensemble *e);
+
+/* ---------------------------------------------------------------------------
+ * Differentiable all-pairs evaluation (FP64, every particle active), for
+ * gradients of fixed-step Hermite trajectories.  All pointers are device
+ * memory; vectors are [n][3] rows, m is [n]; work runs on `stream` (a
+ * cudaStream_t, NULL = legacy default) and is only enqueued.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of device workspace nb_pairs_fp64 needs for n particles (caller
+ * allocated, 256-byte aligned, reusable between calls on one stream). */
+size_t nb_pairs_workspace_bytes(int64_t n);
+
+/* acc, jerk, snap [n][3] of every particle from all others (section 3
+ * item 4) at the given positions x, velocities v and accelerations a.
+ * Errors: NB_EINVAL (n < 1, n > 2^26, NULL pointer, eps out of range), NB_ECUDA. */
+nb_status nb_pairs_fp64(int64_t n, const double *m, const double *x, const double *v,
+                        const double *a, double eps, double *acc, double *jerk, double *snap,
+                        void *work, void *stream);
+
+/* Adjoint of nb_pairs_fp64: given the cotangents gacc, gjerk, gsnap [n][3]
+ * of its outputs, the gradients gx, gv, ga [n][3] and gm [n] of
+ * sum(gacc.acc + gjerk.jerk + gsnap.snap) with respect to x, v, a and m
+ * (hand-written reverse mode of the pair terms, one pass, no atomics).
+ * Errors: NB_EINVAL, NB_ECUDA. */
+nb_status nb_pairs_fp64_adjoint(int64_t n, const double *m, const double *x, const double *v,
+                                const double *a, double eps, const double *gacc,
+                                const double *gjerk, const double *gsnap, double *gx, double *gv,
+                                double *ga, double *gm, void *stream);
 
 /* Allocation-free FP64 evaluation.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory: a host

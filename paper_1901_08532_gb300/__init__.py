@@ -92,6 +92,13 @@ _lib.nb_ensemble_free.restype = None
 for _f in ("nb_ensemble_init", "nb_ensemble_set_shape", "nb_ensemble_run", "nb_ensemble_get_state",
            "nb_ensemble_stats"):
     getattr(_lib, _f).restype = C.c_int
+_lib.nb_pairs_workspace_bytes.argtypes = [C.c_int64]
+_lib.nb_pairs_workspace_bytes.restype = C.c_size_t
+_lib.nb_pairs_fp64.argtypes = [C.c_int64, _vp, _vp, _vp, _vp, C.c_double, _vp, _vp, _vp, _vp, _vp]
+_lib.nb_pairs_fp64.restype = C.c_int
+_lib.nb_pairs_fp64_adjoint.argtypes = [C.c_int64, _vp, _vp, _vp, _vp, C.c_double, _vp, _vp, _vp,
+                                       _vp, _vp, _vp, _vp, _vp]
+_lib.nb_pairs_fp64_adjoint.restype = C.c_int
 _lib.nb_last_error.argtypes = [_vp]
 _lib.nb_last_error.restype = C.c_char_p
 _lib.nb_free.argtypes = [_vp]
@@ -106,7 +113,8 @@ EXPORTED = ("nb_config_default", "nb_init", "nb_predict", "nb_get_predicted", "n
             "nb_get_active", "nb_set_tiles", "nb_resolve_tiles", "nb_counters",
             "nb_evaluate_fp64_static", "nb_last_error", "nb_free", "nb_ensemble_init",
             "nb_ensemble_set_shape", "nb_ensemble_run", "nb_ensemble_get_state", "nb_ensemble_stats",
-            "nb_ensemble_last_error", "nb_ensemble_free")
+            "nb_ensemble_last_error", "nb_ensemble_free", "nb_pairs_workspace_bytes", "nb_pairs_fp64",
+            "nb_pairs_fp64_adjoint")
 
 
 def lib():

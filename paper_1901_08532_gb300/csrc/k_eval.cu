@@ -576,6 +576,40 @@ cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L)
     return cudaGetLastError();
 }
 
+// Stateless all-active FP64 evaluation on caller-packed records (used by the
+// differentiable trajectory path): no split, lanes chosen so the grid holds
+// at least two blocks per SM.
+cudaError_t nb_launch_eval_fp64_rows(const double2 *rec, int n, const int32_t *act, double *out,
+                                     double eps2, nb_ctl *ctl, cudaStream_t stream, int sm_count)
+{
+    cudaError_t e = set_smem_attr(eval_fp64_kernel<1>);
+    if (e != cudaSuccess)
+        return e;
+    const int threads = 128, jt = 128;
+    int lanes = 1;
+    while (lanes < 32 && (static_cast<int64_t>(n) * lanes + threads - 1) / threads < 2 * sm_count)
+        lanes *= 2;
+    const int itile = threads / lanes;
+    EvalArgs a;
+    a.jb = rec;
+    a.n = n;
+    a.act = act;
+    a.n_act = n;
+    a.out = out;
+    a.ostride = n;
+    a.part = nullptr;
+    a.cnt = nullptr;
+    a.jtile = jt;
+    a.lanes = lanes;
+    a.split = 1;
+    a.jchunk = n;
+    a.eps2 = eps2;
+    a.ctl = ctl;
+    const size_t smem = static_cast<size_t>(2) * kRecBytes64 * jt;
+    eval_fp64_kernel<1><<<(n + itile - 1) / itile, threads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------ allocation-free variant
 //
 // For callers that must not allocate device memory, the FP64 evaluation can

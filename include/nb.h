@@ -183,6 +183,15 @@ nb_status nb_set_state(nb_ctx *ctx, const double *x, const double *v,
  * the full count in *n_act. */
 nb_status nb_get_active(nb_ctx *ctx, int32_t *idx, int64_t cap, int64_t *n_act);
 
+/* Test hook for failure detection: kind 1 makes the first shared-memory tile
+ * copy of the NEXT evaluation expect 16 bytes more than the copy delivers,
+ * so that block's bounded wait (1 s of wall clock) runs out; the block
+ * waits, again bounded, for its copies in flight, flags the error and
+ * returns.  The evaluation then reports NB_ETIMEOUT at its next host
+ * synchronisation and the context stays usable.  kind 0 clears it.  The
+ * injection is one-shot. */
+nb_status nb_inject_fault(nb_ctx *ctx, int32_t kind);
+
 /* Replace the evaluation launch shape (zero fields = automatic). */
 nb_status nb_set_tiles(nb_ctx *ctx, const nb_tiles *tiles);
 

@@ -74,6 +74,8 @@ _lib.nb_get_state.argtypes = [_vp] + [_d] * 8
 _lib.nb_set_state.argtypes = [_vp] + [_d] * 8
 _lib.nb_get_active.argtypes = [_vp, _i32, C.c_int64, _i64]
 _lib.nb_set_tiles.argtypes = [_vp, C.POINTER(Tiles)]
+_lib.nb_inject_fault.argtypes = [_vp, C.c_int32]
+_lib.nb_inject_fault.restype = C.c_int
 _lib.nb_resolve_tiles.argtypes = [_vp, C.c_int64, C.POINTER(Tiles)]
 _lib.nb_counters.argtypes = [_vp, _i64, _d]
 _lib.nb_evaluate_fp64_static.argtypes = [_vp, C.c_int64, _vp, C.c_int64, C.c_double, C.c_int32,
@@ -110,7 +112,7 @@ for _f in ("nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_corre
 
 EXPORTED = ("nb_config_default", "nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_correct", "nb_step",
             "nb_run_until", "nb_energy", "nb_angmom", "nb_get_state", "nb_set_state",
-            "nb_get_active", "nb_set_tiles", "nb_resolve_tiles", "nb_counters",
+            "nb_get_active", "nb_set_tiles", "nb_resolve_tiles", "nb_counters", "nb_inject_fault",
             "nb_evaluate_fp64_static", "nb_last_error", "nb_free", "nb_ensemble_init",
             "nb_ensemble_set_shape", "nb_ensemble_run", "nb_ensemble_get_state", "nb_ensemble_stats",
             "nb_ensemble_last_error", "nb_ensemble_free", "nb_pairs_workspace_bytes", "nb_pairs_fp64",
@@ -292,6 +294,10 @@ class NBody:
         idx = np.zeros(max(1, na.value), dtype=np.int32)
         self._check(_lib.nb_get_active(self._ctx, idx.ctypes.data_as(_i32), na.value, C.byref(na)))
         return idx[:na.value]
+
+    def inject_fault(self, kind=1):
+        """Test hook: make the next evaluation's first tile wait run out."""
+        self._check(_lib.nb_inject_fault(self._ctx, int(kind)))
 
     def set_tiles(self, **tiles):
         t = Tiles()

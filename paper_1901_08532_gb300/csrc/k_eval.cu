@@ -17,6 +17,7 @@
 // The self term needs no test: eps > 0 makes r = v = a = 0 contribute 0.
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "nb_device.cuh"
 #include "nb_internal.cuh"
@@ -41,15 +42,16 @@ struct EvalArgs {
     int jtile, lanes, split, jchunk;
     double eps2;
     nb_ctl *ctl;
+    uint32_t tx_extra;   // bytes added to the first tile's expected count (fault injection)
 };
 
 template <int NC>
 __device__ __forceinline__ void issue_tile(unsigned char *smem, uint64_t *bar, const EvalArgs &a,
-                                           int stage, int j0, int len)
+                                           int stage, int j0, int len, uint32_t extra = 0)
 {
     const uint4 *src = static_cast<const uint4 *>(a.jb);
     uint4 *dst = reinterpret_cast<uint4 *>(smem) + static_cast<size_t>(stage) * NC * a.jtile;
-    nbk::mbar_expect_tx(&bar[stage], static_cast<uint32_t>(NC * len * 16));
+    nbk::mbar_expect_tx(&bar[stage], static_cast<uint32_t>(NC * len * 16) + extra);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
         nbk::bulk_g2s(dst + c * a.jtile, src + static_cast<size_t>(c) * a.n + j0,
@@ -154,7 +156,8 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs
         nbk::mbar_init(&bar[1], 1);
         nbk::fence_mbar_init();
         for (; issued < min(2, ntiles); ++issued)
-            issue_tile<NC>(smem, bar, a, issued, jbeg + issued * jt, min(jt, jend - (jbeg + issued * jt)));
+            issue_tile<NC>(smem, bar, a, issued, jbeg + issued * jt, min(jt, jend - (jbeg + issued * jt)),
+                           issued == 0 ? a.tx_extra : 0u);
     }
     __syncthreads();
 
@@ -232,11 +235,11 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs
 
 // 13 bulk copies per tile, one per FP32 row; len and j0 are multiples of 4.
 __device__ __forceinline__ void issue_tile_rows(unsigned char *smem, uint64_t *bar, const EvalArgs &a,
-                                                int stage, int j0, int len)
+                                                int stage, int j0, int len, uint32_t extra = 0)
 {
     const float *src = static_cast<const float *>(a.jb);
     float *dst = reinterpret_cast<float *>(smem) + static_cast<size_t>(stage) * NCF * a.jtile;
-    nbk::mbar_expect_tx(&bar[stage], static_cast<uint32_t>(NCF * len * 4));
+    nbk::mbar_expect_tx(&bar[stage], static_cast<uint32_t>(NCF * len * 4) + extra);
 #pragma unroll
     for (int c = 0; c < NCF; ++c)
         nbk::bulk_g2s(dst + c * a.jtile, src + static_cast<size_t>(c) * a.n + j0,
@@ -294,7 +297,8 @@ __global__ void __launch_bounds__(mixed_max_threads(KI), mixed_min_blocks(KI))
         nbk::mbar_init(&bar[1], 1);
         nbk::fence_mbar_init();
         for (; issued < min(2, ntiles); ++issued)
-            issue_tile_rows(smem, bar, a, issued, jbeg + issued * jt, min(jt, jend - (jbeg + issued * jt)));
+            issue_tile_rows(smem, bar, a, issued, jbeg + issued * jt, min(jt, jend - (jbeg + issued * jt)),
+                            issued == 0 ? a.tx_extra : 0u);
     }
     __syncthreads();
 
@@ -473,21 +477,22 @@ nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req)
         const int64_t nblk = (n_act + itile - 1) / itile;
         const int64_t cap = static_cast<int64_t>(c->sm_count) * resident_blocks(c, t);
         const int64_t max_s = std::max<int64_t>(1, std::min<int64_t>(1024, jn / (2 * t.jtile)));
+        // Each block does 1/s of an i-tile's work, so the launch takes about
+        // ceil(nblk s / cap) / s block-times; take the smallest s within 2 %
+        // of the best (fewer partial sums to fold).
         int64_t best = 1;
-        if (nblk < 2 * cap) {
-            double best_eff = -1.0;
+        if (nblk < 4 * cap) {
+            double tmin = 1e300;
+            std::vector<double> ts(static_cast<size_t>(max_s) + 1, 0.0);
             for (int64_t s = 1; s <= max_s; ++s) {
-                const int64_t blocks = nblk * s;
-                const int64_t waves = (blocks + cap - 1) / cap;
-                const double eff = static_cast<double>(blocks) / static_cast<double>(waves * cap);
-                // prefer fuller waves; among near-equal ones the fewer splits
-                if (eff > best_eff + 0.02) {
-                    best_eff = eff;
-                    best = s;
-                }
-                if (blocks >= 4 * cap)
-                    break;
+                ts[s] = static_cast<double>((nblk * s + cap - 1) / cap) / static_cast<double>(s);
+                tmin = std::min(tmin, ts[s]);
             }
+            for (int64_t s = 1; s <= max_s; ++s)
+                if (ts[s] <= 1.02 * tmin) {
+                    best = s;
+                    break;
+                }
         }
         t.split = static_cast<int32_t>(best);
     }
@@ -534,6 +539,8 @@ cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L)
     a.ctl = c->ctl;
     a.part = nullptr;
     a.cnt = nullptr;
+    a.tx_extra = c->inject == 1 ? 16u : 0u;
+    c->inject = 0;
     if (split > 1) {
         const size_t need = static_cast<size_t>(split) * 9 * L.n_act;
         if (need > c->part_cap) {
@@ -605,6 +612,7 @@ cudaError_t nb_launch_eval_fp64_rows(const double2 *rec, int n, const int32_t *a
     a.jchunk = n;
     a.eps2 = eps2;
     a.ctl = ctl;
+    a.tx_extra = 0;
     const size_t smem = static_cast<size_t>(2) * kRecBytes64 * jt;
     eval_fp64_kernel<1><<<(n + itile - 1) / itile, threads, smem, stream>>>(a);
     return cudaGetLastError();
@@ -739,6 +747,7 @@ extern "C" nb_status nb_evaluate_fp64_static(const void *jrec, int64_t n, const 
     a.jchunk = static_cast<int>(chunk);
     a.eps2 = eps * eps;
     a.ctl = reinterpret_cast<nb_ctl *>(b);
+    a.tx_extra = 0;
     const size_t smem = static_cast<size_t>(2) * kRecBytes64 * jt;
     eval_fp64_kernel<1><<<dim3(static_cast<unsigned>(gx), splits), threads, smem, strm>>>(a);
     e = cudaGetLastError();

@@ -615,6 +615,15 @@ nb_status nb_get_active(nb_ctx *c, int32_t *idx, int64_t cap, int64_t *n_act)
     return NB_OK;
 }
 
+nb_status nb_inject_fault(nb_ctx *c, int32_t kind)
+{
+    CHECK_CTX(c);
+    if (kind != 0 && kind != 1)
+        return fail(c, NB_EINVAL, "fault kind must be 0 (none) or 1 (stalled tile copy)");
+    c->inject = kind;
+    return NB_OK;
+}
+
 nb_status nb_set_tiles(nb_ctx *c, const nb_tiles *tiles)
 {
     CHECK_CTX(c);

@@ -71,6 +71,7 @@ struct nb_ctx {
     double t_sys = 0;          // min t_i after the last block step (host copy)
     int64_t launches = 0;
     double interactions = 0;
+    int32_t inject = 0;        // one-shot fault injection for tests (nb_inject_fault)
     bool dead = false;
     std::string err;
 };
@@ -146,7 +147,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
 
 // Reciprocal square root of a positive normal double: an FP32 hardware
 // estimate (inputs and result converted by exponent re-biasing on the

@@ -81,6 +81,10 @@ def parse():
     p.add_argument("--ens-sample", type=int, default=8,
                    help="systems in the one-at-a-time comparison (0: skip)")
     p.add_argument("--ens-cmp-t-end", type=float, default=0.125)
+    p.add_argument("--integrate", action="store_true",
+                   help="Plummer N=65536 (equal masses, eps 1e-4, seed 2), FP64: one full-N "
+                        "evaluation, then block steps to t = 1/16; interactions/s and the "
+                        "active-set size histogram")
     p.add_argument("--adjoint", action="store_true",
                    help="differentiable fixed-step trajectory: Plummer N=--n (default 8192 in this "
                         "mode), eps 1e-3, dt 2^-10, 64 steps, checkpoints every 8; forward and "
@@ -584,8 +588,57 @@ def adjoint_bench(args):
     return 0
 
 
+def integrate_bench(args):
+    """Plummer N = 65536, FP64 throughout: one full-N evaluation (2^32
+    interactions), then block-step integration to t = 1/16 through
+    nb_run_until (active sets from 1 to N particles)."""
+    import numpy as np
+    import torch
+
+    import nb_inputs as ni
+    import paper_1901_08532_gb300 as nb
+    torch.cuda.set_device(0)
+    n = args.n if args.n != N_BODY else 65536
+    prec = nb.NB_MIXED if args.prec == "mixed" else nb.NB_FP64
+    m, x, v = ni.plummer(n, 2)
+    stream = torch.cuda.current_stream()
+    # dt_max = 2^-4 so that every particle synchronises at t_end = 1/16
+    ctx = nb.NBody(m, x, v, EPS, precision=prec, stream=stream, dt_max=2.0 ** -4)
+    ctx.predict(0.0)
+    ctx.evaluate(None, out=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.evaluate(None, out=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    full_s = e0.elapsed_time(e1) / 1e3
+    E0 = sum(ctx.energy())
+    _, i0 = ctx.counters()
+    t0 = time.perf_counter()
+    steps, (lt, ln) = ctx.run_until(1.0 / 16, log_cap=10 ** 7)
+    el = time.perf_counter() - t0
+    _, i1 = ctx.counters()
+    E1 = sum(ctx.energy())
+    ctx.close()
+    hist = np.bincount(np.floor(np.log2(np.maximum(ln, 1))).astype(int))
+    flops = FLOPS_PER_INTERACTION * float(n) * n / full_s / 1e12
+    peak = PEAK_FP64_TFLOPS if prec == nb.NB_FP64 else PEAK_FP32_TFLOPS
+    print(json.dumps({"workload": f"plummer_N{n}_eps1e-4_{args.prec}", "full_eval_s": full_s,
+                      "full_eval_interactions_per_s": float(n) * n / full_s,
+                      "full_eval_frac_of_peak": flops / peak,
+                      "integration_t_end": 1.0 / 16, "block_steps": steps,
+                      "integration_s": el, "integration_interactions": i1 - i0,
+                      "integration_interactions_per_s": (i1 - i0) / el,
+                      "mean_active": float(ln.mean()), "max_active": int(ln.max()),
+                      "active_log2_histogram": hist.tolist(), "energy_rel_error": abs((E1 - E0) / E0)}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.integrate:
+        return integrate_bench(args)
     if args.adjoint:
         return adjoint_bench(args)
     if args.impl == "reference":

@@ -45,7 +45,8 @@ PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12     # 1.26
 # DRAM traffic of one mixed evaluation launch from an ncu capture of a
 # smaller case, scaled to the full launch; valid only for the kernel source
 # it was measured on (the sha256 prefix of csrc/k_eval.cu).
-TRAFFIC = {"kernel_sha": None, "bytes_per_launch": None, "source": None}
+TRAFFIC = {"kernel_sha": "2bf5d42ec5a41ca4", "bytes_per_launch": 118.36e6 + 69.43e6,
+           "source": "profiles/eval_mixed_dram_plummer_N1048576_all_active.md"}
 WORKLOAD = "plummer_salpeter_N1048576_eps1e-4_shared_step_all_active"
 
 

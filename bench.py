@@ -96,8 +96,10 @@ def parse():
 # ----------------------------------------------------------------- CPU leg
 
 def _oracle_worker(args):
-    """Oracle evaluation of i-rows [lo, hi) of the sample; returns seconds."""
-    lo, hi, n = args
+    """Oracle evaluation of i-rows [lo, hi) of the sample; returns seconds
+    (and, when asked, the sums and their condition numbers, untimed)."""
+    lo, hi, n = args[:3]
+    keep = len(args) > 3 and args[3]
     import numpy as np
 
     import nb_inputs as ni
@@ -106,8 +108,11 @@ def _oracle_worker(args):
     a = np.zeros_like(x)
     act = ni.active_subset(n, 4096, 31)[lo:hi]
     t0 = time.perf_counter()
-    O.evaluate(m, x, v, a, EPS, act)
-    return time.perf_counter() - t0
+    sums = O.evaluate(m, x, v, a, EPS, act)
+    sec = time.perf_counter() - t0
+    if not keep:
+        return sec
+    return sec, act, sums, O.evaluate_kappa(m, x, v, a, EPS, act)
 
 
 def cpu_baseline(n, per_core_rows=48, want_seconds=None):
@@ -116,7 +121,7 @@ def cpu_baseline(n, per_core_rows=48, want_seconds=None):
     4096-particle sample, each i against all n j."""
     import multiprocessing as mp
     cores = len(os.sched_getaffinity(0))
-    t1 = _oracle_worker((0, per_core_rows, n))
+    t1, act, sums, kap = _oracle_worker((0, per_core_rows, n, True))
     one = per_core_rows * n / t1
     ctx = mp.get_context("spawn")
     k = min(cores, 4096 // per_core_rows)
@@ -125,7 +130,7 @@ def cpu_baseline(n, per_core_rows=48, want_seconds=None):
         secs = pool.map(_oracle_worker, jobs)
     allc = k * per_core_rows * n / max(secs)   # instances run concurrently
     return {"value": allc, "unit": "interactions/s", "cores": k, "kind": "oracle",
-            "one_core": one,
+            "one_core": one, "_ref": (act, sums, kap),
             "sample": f"{k} oracle instances x {per_core_rows} i-particles of a seeded 4096-i "
                       f"subset x all {n} j (FP64, single-threaded C); one-core run: "
                       f"{per_core_rows} i x {n} j in {t1:.1f} s",
@@ -313,6 +318,9 @@ def run_ours(args):
 
     e2e = end_to_end(nb, np, torch, mixed, n, stream, max(1, min(args.steps, 3)))
     mixed.close()
+    err_oracle = None
+    if cpu is not None:
+        err_oracle = error_vs_oracle(nb, np, torch, m, x, v, stream, *cpu.pop("_ref"))
 
     line = {
         "metric": "acc+jerk+snap interactions/s at N=2^20, mixed vs FP64 at rel err <= 1e-6",
@@ -339,6 +347,8 @@ def run_ours(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if err_oracle is not None:
+        line["err_vs_oracle"] = err_oracle
     line.update(extra)
     if rank == 0:
         print(json.dumps(line))
@@ -408,6 +418,27 @@ def secondary(nb, np, torch, m, x, v, st, stream, n):
     out["speedup_mixed_over_fp64"] = mixed_rate / fr["fp64_2^-5"]["interactions_per_s"]
     fp64.close()
     mixed.close()
+    return out
+
+
+def error_vs_oracle(nb, np, torch, m, x, v, stream, act, sums, kap):
+    """Both GPU precisions on the oracle's sample (same inputs: a = 0 at
+    t = 0): per particle |d|_inf / |ref|_2, and |d|_inf / sum_j |T_ij| (the
+    error relative to the sum's condition number)."""
+    out = {"sample": int(len(act)), "inputs": "start positions and velocities, a = 0"}
+    for name, prec in (("mixed", nb.NB_MIXED), ("fp64", nb.NB_FP64)):
+        ctx = nb.NBody(m, x, v, EPS, precision=prec, stream=stream, start_forces=False)
+        ctx.predict(0.0)
+        got = ctx.evaluate(act)
+        ctx.close()
+        rec = {}
+        for q, g, r, k in zip(("acc", "jerk", "snap"), got, sums, kap):
+            d = np.abs(g - r).max(axis=1)
+            rec[q] = {"max": float((d / np.linalg.norm(r, axis=1)).max()),
+                      "kappa_norm_max": float((d / k).max())}
+        out[name] = rec
+    out["mixed_within_1e-6_of_condition_number"] = all(
+        out["mixed"][q]["kappa_norm_max"] <= 1e-6 for q in ("acc", "jerk", "snap"))
     return out
 
 

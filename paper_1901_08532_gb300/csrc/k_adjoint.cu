@@ -25,9 +25,7 @@
 // Particle k receives -dL/d(r, v, a) of every pair where it is i (with its
 // own cotangents) and +dL/d(r, v, a) and dL/dm of every pair where it is j
 // (with the other particle's cotangents); one thread owns k and visits every
-// l once, so no atomics are needed.  The i = j terms of the two roles are
-// equal and opposite and are combined before accumulation, so they cancel
-// exactly.
+// l once, so no atomics are needed.
 #include <algorithm>
 
 #include "nb_device.cuh"
@@ -38,43 +36,43 @@ namespace {
 constexpr int kAdjThreads = 128;
 constexpr int kAdjTile = 64;
 
-struct PairGrad {
-    double r[3], v[3], a[3], m;
-};
-
-// dL/d(r, v, a) and dL/dm_j for one pair and one set of cotangents.
-__device__ __forceinline__ void pair_vjp(const double (&r)[3], const double (&v)[3], const double (&a)[3],
-                                         double mj, double q, double q2, double al, double be,
-                                         const double *gb, PairGrad &out)
+// The bracket B(g) of dL/d(r, v, a) = q^3 B(g) for a pair with unit source
+// mass (mu = m_j q^3 factored out), linear in the cotangents g.
+__device__ __forceinline__ void pair_bracket(const double (&r)[3], const double (&v)[3], const double (&a)[3],
+                                             const double (&u)[3], const double (&w)[3], double q2, double al,
+                                             double be, const double *g, double (&br)[3], double (&bv)[3],
+                                             double (&ba)[3])
 {
-    const double *Ab = gb, *Jb = gb + 3, *Sb = gb + 6;
-    const double mu = mj * q * q2;
+    const double *Ab = g, *Jb = g + 3, *Sb = g + 6;
     const double c18 = 18.0 * al * al - 3.0 * be;
-    double Pr[3], u[3], w[3];
     double phi = 0, sr = 0, sv = 0, jr = 0;
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-        Pr[d] = Ab[d] - 3.0 * al * Jb[d] + c18 * Sb[d];
-        u[d] = v[d] - 3.0 * al * r[d];
+        phi = fma(Ab[d], r[d], fma(Jb[d], u[d], fma(Sb[d], w[d], phi)));
         sr = fma(Sb[d], r[d], sr);
         sv = fma(Sb[d], v[d], sv);
         jr = fma(Jb[d], r[d], jr);
     }
-    for (int d = 0; d < 3; ++d) {
-        w[d] = a[d] - 6.0 * al * u[d] - 3.0 * be * r[d];
-        phi += Ab[d] * r[d] + Jb[d] * u[d] + Sb[d] * w[d];
-    }
     const double Pa = -3.0 * jr - 6.0 * sv + 36.0 * al * sr;
     const double Pb = -3.0 * sr;
-    const double cv = Pa + 2.0 * al * Pb;
-    const double cr = 3.0 * phi + 2.0 * al * Pa + 2.0 * (be + al * al) * Pb;
+    const double cv = fma(2.0 * al, Pb, Pa);
+    const double cr = fma(3.0, phi, fma(2.0 * al, Pa, 2.0 * (be + al * al) * Pb));
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-        out.r[d] = mu * (Pr[d] + q2 * (cv * v[d] + Pb * a[d] - cr * r[d]));
-        out.v[d] = mu * (Jb[d] - 6.0 * al * Sb[d] + q2 * (cv * r[d] + 2.0 * Pb * v[d]));
-        out.a[d] = mu * (Sb[d] + q2 * Pb * r[d]);
+        const double Pr = fma(c18, Sb[d], fma(-3.0 * al, Jb[d], Ab[d]));
+        br[d] = fma(q2, fma(cv, v[d], fma(Pb, a[d], -cr * r[d])), Pr);
+        bv[d] = fma(q2, fma(cv, r[d], 2.0 * Pb * v[d]), fma(-6.0 * al, Sb[d], Jb[d]));
+        ba[d] = fma(q2 * Pb, r[d], Sb[d]);
     }
-    out.m = q * q2 * phi;
 }
 
+// For particle k and every l: the pair (i = k, j = l) with k's cotangents and
+// source mass m_l, and the pair (i = l, j = k) with l's cotangents and source
+// mass m_k.  Negating r, v, a negates u, w, Phi and the bracket's
+// coefficients, so the second pair's gradient with respect to x_k equals the
+// first pair's form evaluated at (r, v, a) with l's cotangents; by linearity
+// both roles need one bracket with g* = m_k g_l - m_l g_k, times q^3.  The mass
+// gradient of m_k is -q^3 Phi(g_l).  For l = k, g* = 0 and Phi = 0 exactly.
 __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(int n, const double *__restrict__ m,
                                                               const double *__restrict__ x,
                                                               const double *__restrict__ v,
@@ -120,7 +118,6 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(int n, const doubl
         __syncthreads();
         const int len = min(kAdjTile, n - l0);
         for (int e = 0; e < len; ++e) {
-            // pair (i = k, j = l): r = x_l - x_k
             double r[3], vr[3], ar[3];
             for (int d = 0; d < 3; ++d) {
                 r[d] = s_st[e][d] - xk[d];
@@ -128,25 +125,32 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(int n, const doubl
                 ar[d] = s_st[e][6 + d] - ak[d];
             }
             const double R = fma(r[0], r[0], fma(r[1], r[1], fma(r[2], r[2], eps2)));
-            const double q = 1.0 / sqrt(R);
-            const double q2 = q * q;
-            const double al = (r[0] * vr[0] + r[1] * vr[1] + r[2] * vr[2]) * q2;
-            const double be = (vr[0] * vr[0] + vr[1] * vr[1] + vr[2] * vr[2] + r[0] * ar[0] +
-                               r[1] * ar[1] + r[2] * ar[2]) * q2 + al * al;
-            PairGrad as_i, as_j;
-            // k as i: cotangents of k, source mass m_l
-            pair_vjp(r, vr, ar, s_st[e][9], q, q2, al, be, gk, as_i);
-            // k as j in the pair (i = l, j = k): differences negate, alpha and
-            // beta are unchanged, source mass m_k, cotangents of l
-            double nr[3] = {-r[0], -r[1], -r[2]}, nv[3] = {-vr[0], -vr[1], -vr[2]},
-                   na[3] = {-ar[0], -ar[1], -ar[2]};
-            pair_vjp(nr, nv, na, mk, q, q2, al, be, s_g[e], as_j);
+            const double q = nbk::rsqrt_fp64(R);
+            const double q2 = q * q, q3 = q * q2;
+            const double al = fma(r[0], vr[0], fma(r[1], vr[1], r[2] * vr[2])) * q2;
+            const double be = fma(fma(vr[0], vr[0], fma(vr[1], vr[1], vr[2] * vr[2])) +
+                                      fma(r[0], ar[0], fma(r[1], ar[1], r[2] * ar[2])),
+                                  q2, al * al);
+            double u[3], w[3];
             for (int d = 0; d < 3; ++d) {
-                ox[d] += as_j.r[d] - as_i.r[d];
-                ov[d] += as_j.v[d] - as_i.v[d];
-                oa[d] += as_j.a[d] - as_i.a[d];
+                u[d] = fma(-3.0 * al, r[d], vr[d]);
+                w[d] = fma(-6.0 * al, u[d], fma(-3.0 * be, r[d], ar[d]));
             }
-            om += as_j.m;
+            const double ml = s_st[e][9];
+            double gs[9];
+            double phil = 0.0;
+            for (int q9 = 0; q9 < 9; ++q9)
+                gs[q9] = fma(mk, s_g[e][q9], -ml * gk[q9]);
+            for (int d = 0; d < 3; ++d)
+                phil = fma(s_g[e][d], r[d], fma(s_g[e][3 + d], u[d], fma(s_g[e][6 + d], w[d], phil)));
+            double br[3], bv[3], ba[3];
+            pair_bracket(r, vr, ar, u, w, q2, al, be, gs, br, bv, ba);
+            for (int d = 0; d < 3; ++d) {
+                ox[d] = fma(q3, br[d], ox[d]);
+                ov[d] = fma(q3, bv[d], ov[d]);
+                oa[d] = fma(q3, ba[d], oa[d]);
+            }
+            om = fma(-q3, phil, om);
         }
     }
     if (valid) {

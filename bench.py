@@ -77,8 +77,8 @@ def parse():
                         "(seed 4), each to --ens-t-end; one persistent launch vs one at a time")
     p.add_argument("--ens-t-end", type=float, default=0.25)
     p.add_argument("--ens-systems", type=int, default=256)
-    p.add_argument("--ens-shapes", default="8x256",
-                   help="comma-separated ctas_per_system x threads shapes to time")
+    p.add_argument("--ens-shapes", default="4x256",
+                   help="comma-separated ctas_per_system x threads [x jtile] shapes to time")
     p.add_argument("--ens-sample", type=int, default=8,
                    help="systems in the one-at-a-time comparison (0: skip)")
     p.add_argument("--ens-cmp-t-end", type=float, default=0.125)
@@ -90,6 +90,13 @@ def parse():
                    help="differentiable fixed-step trajectory: Plummer N=--n (default 8192 in this "
                         "mode), eps 1e-3, dt 2^-10, 64 steps, checkpoints every 8; forward and "
                         "backward times")
+    p.add_argument("--precision-study", action="store_true",
+                   help="energy and angular-momentum errors against time (Eq. 1) for FP64, mixed "
+                        "and single-precision positions: Plummer N=--n (default 4096 in this mode), "
+                        "equal masses, eps 1e-4, block steps, a device sample every --ps-dt")
+    p.add_argument("--ps-t-end", type=float, default=1.0)
+    p.add_argument("--ps-dt", type=float, default=2.0 ** -3)
+    p.add_argument("--ps-precs", default="fp64,mixed,sp")
     return p.parse_args()
 
 
@@ -530,9 +537,9 @@ def ensemble_bench(args):
                 np.concatenate([parts[k][2] for k in idx]))
 
     def run_ens(idx, prec, shape, t_end):
-        g, thr = shape
+        g, thr, jt = shape
         ens = nb.Ensemble(sizes[idx], *cat(idx), EPS, precision=prec)
-        ens.set_shape(g, thr)
+        ens.set_shape(g, thr, jt or None)
         _, it0, _ = ens.stats()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -547,13 +554,14 @@ def ensemble_bench(args):
            "systems": int(sizes.size), "particles": int(sizes.sum())}
     precs = ("mixed", "fp64") if args.prec == "both" else (args.prec,)
     shapes = [tuple(int(q) for q in sh.split("x")) for sh in args.ens_shapes.split(",")]
+    shapes = [sh if len(sh) == 3 else (sh[0], sh[1], 0) for sh in shapes]
     everyone = list(range(sizes.size))
     for prec_name in precs:
         prec = nb.NB_MIXED if prec_name == "mixed" else nb.NB_FP64
         res = {"t_end": args.ens_t_end, "shapes": {}}
         for sh in shapes:
             r = run_ens(everyone, prec, sh, args.ens_t_end)
-            res["shapes"]["%dx%d" % sh] = r
+            res["shapes"]["%dx%dx%d" % sh] = r
             print(json.dumps({"progress": prec_name, "shape": sh, **r}), flush=True)
         best_shape = max(res["shapes"], key=lambda k: res["shapes"][k]["interactions_per_s"])
         res["best_shape"] = best_shape
@@ -667,8 +675,50 @@ def integrate_bench(args):
     return 0
 
 
+def precision_study(args):
+    """The precision experiment of section 3 item 6: the same Plummer system
+    integrated with block steps in each arithmetic, sampling the energy and
+    the angular momentum on the device (nb_run_diag) and reporting
+    dE/E = |E_start - E(t)| / |E_start| and dL/L = |L_start - L(t)| / |L_start|
+    (Eq. 1; L the vector, also relative to sum m |x cross v| because the net
+    L of an isotropic model is small)."""
+    import numpy as np
+    import torch
+
+    import nb_inputs as ni
+    import paper_1901_08532_gb300 as nb
+    torch.cuda.set_device(0)
+    n = args.n if args.n != N_BODY else 4096
+    m, x, v = ni.plummer(n, 1)
+    precs = {"fp64": nb.NB_FP64, "mixed": nb.NB_MIXED, "sp": nb.NB_SP}
+    res = {"workload": f"precision_study_plummer_N{n}_equal_eps1e-4_t{args.ps_t_end:g}",
+           "sample_dt": args.ps_dt, "t_end": args.ps_t_end}
+    for name in args.ps_precs.split(","):
+        ctx = nb.NBody(m, x, v, EPS, precision=precs[name], dt_max=args.ps_dt)
+        t0 = time.perf_counter()
+        steps, d = ctx.run_diag(args.ps_t_end, args.ps_dt)
+        el = time.perf_counter() - t0
+        _, inter = ctx.counters()
+        ctx.close()
+        E = d["ekin"] + d["epot"]
+        dE = np.abs(E[0] - E) / abs(E[0])
+        dL = np.linalg.norm(d["L"] - d["L"][0], axis=1)
+        res[name] = {"block_steps": steps, "seconds": el, "interactions": inter,
+                     "t": d["t"].tolist(), "dE_over_E": dE.tolist(),
+                     "dL_over_L": (dL / np.linalg.norm(d["L"][0])).tolist(),
+                     "dL_over_sum_m_xv": (dL / d["labs"][0]).tolist(),
+                     "max_dE_over_E": float(dE.max()), "final_dE_over_E": float(dE[-1])}
+        print(json.dumps({"prec": name, "block_steps": steps, "seconds": el,
+                          "max_dE_over_E": float(dE.max()), "final_dE_over_E": float(dE[-1]),
+                          "final_dL_over_L": res[name]["dL_over_L"][-1]}), flush=True)
+    print(json.dumps(res))
+    return 0
+
+
 def main():
     args = parse()
+    if args.precision_study:
+        return precision_study(args)
     if args.integrate:
         return integrate_bench(args)
     if args.adjoint:

@@ -61,21 +61,36 @@ typedef enum {
  * correction, time steps and energy are FP64 in both modes. */
 typedef enum {
     NB_FP64 = 0,  /* every operation of the pair sum in IEEE double          */
-    NB_MIXED = 1  /* FP64 positions and accumulation; pair differences
+    NB_MIXED = 1, /* FP64 positions and accumulation; pair differences
                      rounded to FP32 (positions as hi + lo FP32 pairs), FP32
                      rsqrt and pair arithmetic, FP32 sums within a j-tile
                      folded into a compensated (TwoSum) accumulator         */
+    NB_SP = 2,    /* single precision control (section 3 item 6): as NB_MIXED
+                     but positions rounded to FP32 (no lo part), so pair
+                     differences carry the rounding of the positions; not
+                     available for ensembles                                 */
+    NB_EX = 3     /* extended precision (section 3 item 6): every predicted
+                     position, velocity, acceleration and mass held as a
+                     double word hi + lo of FP32 numbers (about 48 mantissa
+                     bits, FP32 exponent range) and the whole pair term
+                     computed in double-word arithmetic from FP32
+                     operations; per-tile sums added in FP64; not available
+                     for ensembles                                           */
 } nb_precision;
 
 /* Shape of the evaluation launch.  0 in any field means "choose
  * automatically". */
 typedef struct {
-    int32_t ki;       /* i-particles per thread: 1, 2 or 4 (mixed: 1 or 2)    */
-    int32_t threads;  /* threads per block: 32..512, multiple of 32            */
+    int32_t ki;       /* i-particles per thread: 1, 2 or 4 (mixed: 1 or 2;
+                         EX: 1)                                               */
+    int32_t threads;  /* threads per block: 32..512, multiple of 32 (EX:
+                         at most 128)                                         */
     int32_t jtile;    /* j-particles per shared-memory stage: multiple of lanes */
     int32_t lanes;    /* threads sharing one i (j split inside a warp): 1..32  */
     int32_t split;    /* blocks sharing one i-tile (j split across blocks)     */
-    int32_t junroll;  /* mixed path: j per inner iteration, 2 or 4            */
+    int32_t junroll;  /* mixed path: j per inner iteration, 2 or 4; EX: 2
+                         (two j in the lanes of packed f32x2 operations) or 1
+                         (scalar FP32 operations)                             */
 } nb_tiles;
 
 typedef struct {
@@ -118,8 +133,10 @@ nb_status nb_predict(nb_ctx *ctx, double t);
 
 /* Read back the evaluation buffer written by the last nb_predict: predicted
  * positions, velocities and accelerations ([n][3] host arrays; NULL skips).
- * NB_FP64 contexts return the FP64 values; NB_MIXED contexts return the
- * FP32 values the mixed kernel uses (position = hi + lo, evaluated in FP64).
+ * NB_FP64 contexts return the FP64 values; NB_MIXED and NB_SP contexts
+ * return the FP32 values the packed FP32 kernel uses (position = hi + lo,
+ * evaluated in FP64; lo = 0 for NB_SP); NB_EX contexts return hi + lo of
+ * every double word.
  * Errors: NB_ESTATE (no prediction yet). */
 nb_status nb_get_predicted(nb_ctx *ctx, double *xp, double *vp, double *ap);
 
@@ -157,6 +174,25 @@ nb_status nb_step(nb_ctx *ctx, double *t_out, int64_t *n_act_out);
  * and log_n[] (active count). */
 nb_status nb_run_until(nb_ctx *ctx, double t_end, int64_t *steps_out,
                        int64_t log_cap, double *log_t, int64_t *log_n);
+
+/* Integrate like nb_run_until and record a diagnostics stream on the device
+ * (section 3 item 3: energy and angular momentum are computed on the device;
+ * Eq. 1 defines their relative errors).  A sample is taken at the starting
+ * time and at every multiple of dt_diag up to t_end, when all particles are
+ * synchronised; samples stay in device memory during the run and are copied
+ * to the host once at the end.
+ *   dt_diag  > 0, a multiple of dt_max (dt_shared in shared mode); t_end a
+ *            multiple of dt_diag; the current time must be a multiple of
+ *            dt_max (true after nb_init and after any nb_run_until /
+ *            nb_run_diag).
+ *   cap      capacity of out in samples; samples beyond cap are computed but
+ *            not returned (*n_samples still counts them).
+ *   out      host array [cap][8], per sample: t, E_kin, E_pot, L_x, L_y, L_z,
+ *            sum m |x cross v|, number of block steps taken so far.
+ *   n_samples, steps_out  may be NULL.
+ * Errors: NB_EINVAL for the conditions above, then as nb_run_until. */
+nb_status nb_run_diag(nb_ctx *ctx, double t_end, double dt_diag, int64_t cap, double *out,
+                      int64_t *n_samples, int64_t *steps_out);
 
 /* Kinetic energy sum 1/2 m v^2 and softened potential
  * -sum_{i<j} m_i m_j / sqrt(r^2 + eps^2) of the current state (section 3

@@ -29,7 +29,7 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 NB_OK, NB_EINVAL, NB_ECUDA, NB_ENOMEM, NB_ENONFINITE, NB_ETIMEOUT, NB_ESTATE = 0, -1, -2, -3, -4, -5, -6
-NB_FP64, NB_MIXED = 0, 1
+NB_FP64, NB_MIXED, NB_SP, NB_EX = 0, 1, 2, 3
 _STATUS = {NB_EINVAL: "NB_EINVAL", NB_ECUDA: "NB_ECUDA", NB_ENOMEM: "NB_ENOMEM",
            NB_ENONFINITE: "NB_ENONFINITE", NB_ETIMEOUT: "NB_ETIMEOUT", NB_ESTATE: "NB_ESTATE"}
 
@@ -68,6 +68,7 @@ _lib.nb_evaluate.argtypes = [_vp, _vp, C.c_int64, C.c_int, _vp, _vp, _vp, C.c_in
 _lib.nb_correct.argtypes = [_vp, C.c_double]
 _lib.nb_step.argtypes = [_vp, _d, _i64]
 _lib.nb_run_until.argtypes = [_vp, C.c_double, _i64, C.c_int64, _d, _i64]
+_lib.nb_run_diag.argtypes = [_vp, C.c_double, C.c_double, C.c_int64, _d, _i64, _i64]
 _lib.nb_energy.argtypes = [_vp, _d, _d]
 _lib.nb_angmom.argtypes = [_vp, _d, _d]
 _lib.nb_get_state.argtypes = [_vp] + [_d] * 8
@@ -106,12 +107,13 @@ _lib.nb_last_error.restype = C.c_char_p
 _lib.nb_free.argtypes = [_vp]
 _lib.nb_free.restype = None
 for _f in ("nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_correct", "nb_step", "nb_run_until",
+           "nb_run_diag",
            "nb_energy", "nb_angmom", "nb_get_state", "nb_set_state", "nb_get_active",
            "nb_set_tiles", "nb_resolve_tiles", "nb_counters"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("nb_config_default", "nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_correct", "nb_step",
-            "nb_run_until", "nb_energy", "nb_angmom", "nb_get_state", "nb_set_state",
+            "nb_run_until", "nb_run_diag", "nb_energy", "nb_angmom", "nb_get_state", "nb_set_state",
             "nb_get_active", "nb_set_tiles", "nb_resolve_tiles", "nb_counters", "nb_inject_fault",
             "nb_evaluate_fp64_static", "nb_last_error", "nb_free", "nb_ensemble_init",
             "nb_ensemble_set_shape", "nb_ensemble_run", "nb_ensemble_get_state", "nb_ensemble_stats",
@@ -153,7 +155,7 @@ class NBody:
     """One N-body system on the current CUDA device (a libnb context).
 
     m[n], x[n,3], v[n,3] are host arrays (copied); eps > 0.  precision is
-    NB_FP64 or NB_MIXED.  stream: a torch.cuda.Stream or raw cudaStream_t
+    NB_FP64, NB_MIXED, NB_SP or NB_EX (the last two NBody only).  stream: a torch.cuda.Stream or raw cudaStream_t
     (default: torch's current stream).
     """
 
@@ -257,6 +259,24 @@ class NBody:
         k = min(int(steps.value), log_cap)
         return int(steps.value), (lt[:k], ln[:k])
 
+    def run_diag(self, t_end, dt_diag, cap=None):
+        """Integrate to t_end, sampling energy and angular momentum on the
+        device at the current time and every multiple of dt_diag.  Returns
+        (steps, samples) with samples a dict of arrays: t, ekin, epot, L [k, 3],
+        labs, steps."""
+        if cap is None:
+            cap = int(t_end / dt_diag) + 1 if dt_diag > 0 else 1
+        cap = max(1, cap)
+        out = np.zeros((cap, 8))
+        ns, steps = C.c_int64(), C.c_int64()
+        self._check(_lib.nb_run_diag(self._ctx, float(t_end), float(dt_diag), cap, _ptr(out),
+                                     C.byref(ns), C.byref(steps)))
+        k = min(cap, int(ns.value))
+        o = out[:k]
+        return int(steps.value), {"t": o[:, 0].copy(), "ekin": o[:, 1].copy(), "epot": o[:, 2].copy(),
+                                  "L": o[:, 3:6].copy(), "labs": o[:, 6].copy(),
+                                  "steps": o[:, 7].astype(np.int64)}
+
     # --- diagnostics and state ---------------------------------------------
     def energy(self):
         ek, ep = C.c_double(), C.c_double()
@@ -352,7 +372,7 @@ class Ensemble:
 
     def set_shape(self, ctas_per_system=8, threads=256, jtile=None):
         if jtile is None:
-            jtile = 256 if self.precision == NB_MIXED else 128
+            jtile = 1024 if self.precision == NB_MIXED else 512
         self._check(_lib.nb_ensemble_set_shape(self._e, int(ctas_per_system), int(threads), int(jtile)))
 
     def run(self, t_end, use_graph=True):

@@ -29,11 +29,11 @@ def _bucket(n_act: int) -> int:
 
 
 def candidates(precision: int):
-    space = MIXED_SPACE if precision == 1 else FP64_SPACE
+    space = MIXED_SPACE if precision in (1, 2) else FP64_SPACE
     keys = sorted(space)
     for vals in itertools.product(*(space[k] for k in keys)):
         shape = dict(zip(keys, vals))
-        if precision == 1 and shape["ki"] == 2 and shape["threads"] > 128:
+        if precision in (1, 2) and shape["ki"] == 2 and shape["threads"] > 128:
             continue
         if shape["ki"] == 2 and shape["threads"] > 256:
             continue

@@ -726,7 +726,7 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
     e->eps = eps;
     e->nc = n_systems;
     e->P = padded;
-    e->jtile = cf.precision == NB_MIXED ? 256 : 128;
+    e->jtile = cf.precision == NB_MIXED ? 1024 : 512;
     auto bail = [&](nb_status s) {
         nb_set_thread_error(e->err.c_str());
         ens_free_all(e);

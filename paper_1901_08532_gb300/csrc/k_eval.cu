@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "nb_device.cuh"
+#include "nb_ff.cuh"
 #include "nb_internal.cuh"
 
 namespace {
@@ -233,15 +234,16 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs
 // FP32 (two halves), then folds the tile sum into a TwoSum-compensated
 // (hi, lo) accumulator.
 
-// 13 bulk copies per tile, one per FP32 row; len and j0 are multiples of 4.
+// NR bulk copies per tile, one per FP32 row; len and j0 are multiples of 4.
+template <int NR = NCF>
 __device__ __forceinline__ void issue_tile_rows(unsigned char *smem, uint64_t *bar, const EvalArgs &a,
                                                 int stage, int j0, int len, uint32_t extra = 0)
 {
     const float *src = static_cast<const float *>(a.jb);
-    float *dst = reinterpret_cast<float *>(smem) + static_cast<size_t>(stage) * NCF * a.jtile;
-    nbk::mbar_expect_tx(&bar[stage], static_cast<uint32_t>(NCF * len * 4) + extra);
+    float *dst = reinterpret_cast<float *>(smem) + static_cast<size_t>(stage) * NR * a.jtile;
+    nbk::mbar_expect_tx(&bar[stage], static_cast<uint32_t>(NR * len * 4) + extra);
 #pragma unroll
-    for (int c = 0; c < NCF; ++c)
+    for (int c = 0; c < NR; ++c)
         nbk::bulk_g2s(dst + c * a.jtile, src + static_cast<size_t>(c) * a.n + j0,
                       static_cast<uint32_t>(len * 4), &bar[stage]);
 }
@@ -390,8 +392,112 @@ __global__ void __launch_bounds__(mixed_max_threads(KI), mixed_min_blocks(KI))
     store_or_fold<KI>(a, acc, kidx, lj, slots, ibase);
 }
 
+// -------------------------------------------------------------------- EX
+//
+// Double-word ("float-float") pair arithmetic from FP32 operations only
+// (section 3 item 6): the j-tile holds 20 FP32 rows (every position,
+// velocity, acceleration and mass as a high and a low part), each pair term
+// is formed with the error-free transformations of nb_ff.cuh, a thread sums
+// the terms of one tile in unnormalised double words (Sum2), and each
+// tile's sum is added to an FP64 total.  T = float2 evaluates two j per
+// instruction in the lanes of the packed f32x2 operations, T = float one.
+// One i-particle per thread slot.
+
+constexpr int kExThreads = 128;
+
+template <class T>
+__global__ void __launch_bounds__(kExThreads, 2) eval_ex_kernel(EvalArgs a)
+{
+    using ff::FF;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    constexpr int JU = sizeof(T) / sizeof(float);
+    const int tid = threadIdx.x, lanes = a.lanes, jt = a.jtile;
+    const int slot = tid / lanes, lj = tid - slot * lanes;
+    const int slots = blockDim.x / lanes;
+    const int ibase = blockIdx.x * slots;
+    const float *jf = static_cast<const float *>(a.jb);
+    const size_t np = static_cast<size_t>(a.n);
+    const T z = ff::splat(T{}, 0.0f);
+    const float e2h = __double2float_rn(a.eps2);
+    const FF<T> eps2 = {ff::splat(z, e2h), ff::splat(z, __double2float_rn(a.eps2 - static_cast<double>(e2h)))};
+
+    int kidx[1];
+    const int p = ibase + slot;
+    kidx[0] = p < a.n_act ? p : -1;
+    const int i = a.act[p < a.n_act ? p : a.n_act - 1];
+    ExI<T> ni;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        ni.x[k] = {ff::splat(z, -jf[k * np + i]), ff::splat(z, -jf[(3 + k) * np + i])};
+        ni.v[k] = {ff::splat(z, -jf[(6 + k) * np + i]), ff::splat(z, -jf[(9 + k) * np + i])};
+        ni.a[k] = {ff::splat(z, -jf[(12 + k) * np + i]), ff::splat(z, -jf[(15 + k) * np + i])};
+    }
+    double acc[9][1];
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+        acc[q][0] = 0.0;
+
+    const int jbeg = blockIdx.y * a.jchunk;
+    const int jend = min(a.n, jbeg + a.jchunk);
+    const int ntiles = jend > jbeg ? (jend - jbeg + jt - 1) / jt : 0;
+    int issued = 0;
+    if (tid == 0) {
+        nbk::mbar_init(&bar[0], 1);
+        nbk::mbar_init(&bar[1], 1);
+        nbk::fence_mbar_init();
+        for (; issued < min(2, ntiles); ++issued)
+            issue_tile_rows<NCX>(smem, bar, a, issued, jbeg + issued * jt,
+                                 min(jt, jend - (jbeg + issued * jt)), issued == 0 ? a.tx_extra : 0u);
+    }
+    __syncthreads();
+
+    for (int tl = 0; tl < ntiles; ++tl) {
+        const int st = tl & 1;
+        const bool ok = nbk::mbar_wait_bounded(&bar[st], (tl >> 1) & 1, nbk::kWaitLimitNs);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0)
+                drain_after_timeout(bar, tl, issued, a.ctl);
+            return;
+        }
+        const int len = min(jt, jend - (jbeg + tl * jt));
+        const float *s = reinterpret_cast<const float *>(smem) + static_cast<size_t>(st) * NCX * jt;
+        FF<T> part[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            part[q] = {z, z};
+        for (int jj = JU * lj; jj < len; jj += JU * lanes) {
+            T c[NCX];
+#pragma unroll
+            for (int r = 0; r < NCX; ++r)
+                c[r] = *reinterpret_cast<const T *>(s + r * jt + jj);
+            pair_ex(c, ni, eps2, part);
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float *h = reinterpret_cast<const float *>(&part[q].h);
+            const float *l = reinterpret_cast<const float *>(&part[q].l);
+#pragma unroll
+            for (int u = 0; u < JU; ++u)
+                acc[q][0] += static_cast<double>(h[u]) + static_cast<double>(l[u]);
+        }
+        __syncthreads();
+        if (tid == 0 && tl + 2 < ntiles) {
+            issue_tile_rows<NCX>(smem, bar, a, st, jbeg + (tl + 2) * jt, min(jt, jend - (jbeg + (tl + 2) * jt)));
+            ++issued;
+        }
+    }
+
+    for (int off = lanes >> 1; off > 0; off >>= 1)
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            acc[q][0] += __shfl_xor_sync(0xffffffffu, acc[q][0], off);
+    store_or_fold<1>(a, acc, kidx, lj, slots, ibase);
+}
+
 constexpr int kRecBytes64 = 5 * 16;
 constexpr int kRecBytes32 = NCF * 4;
+constexpr int kRecBytesEx = NCX * 4;
 
 template <typename K>
 cudaError_t set_smem_attr(K kernel)
@@ -412,18 +518,24 @@ cudaError_t nb_eval_smem_setup()
     if ((e = set_smem_attr(eval_mixed_kernel<1, 2>)) != cudaSuccess) return e;
     if ((e = set_smem_attr(eval_mixed_kernel<1, 4>)) != cudaSuccess) return e;
     if ((e = set_smem_attr(eval_mixed_kernel<2, 2>)) != cudaSuccess) return e;
+    if ((e = set_smem_attr(eval_ex_kernel<float>)) != cudaSuccess) return e;
+    if ((e = set_smem_attr(eval_ex_kernel<float2>)) != cudaSuccess) return e;
     return set_smem_attr(eval_mixed_kernel<2, 4>);
 }
 
 // Blocks of the chosen evaluation kernel that fit on one SM.
 int resident_blocks(const nb_ctx *c, const nb_tiles &t)
 {
-    const bool mixed = c->cfg.precision == NB_MIXED;
-    const size_t smem = static_cast<size_t>(2) * (mixed ? kRecBytes32 : kRecBytes64) * t.jtile +
+    const bool mixed = nb_fp32_eval(c->cfg.precision);
+    const bool ex = c->cfg.precision == NB_EX;
+    const size_t smem = static_cast<size_t>(2) * (ex ? kRecBytesEx : mixed ? kRecBytes32 : kRecBytes64) * t.jtile +
                         (mixed ? static_cast<size_t>(18) * t.ki * t.threads * sizeof(float) : 0);
     int nb = 0;
     cudaError_t e;
-    if (mixed) {
+    if (ex) {
+        if (t.junroll == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_ex_kernel<float>, t.threads, smem);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_ex_kernel<float2>, t.threads, smem);
+    } else if (mixed) {
         if (t.ki == 1 && t.junroll == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_mixed_kernel<1, 2>, t.threads, smem);
         else if (t.ki == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_mixed_kernel<1, 4>, t.threads, smem);
         else if (t.junroll == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_mixed_kernel<2, 2>, t.threads, smem);
@@ -447,7 +559,8 @@ int resident_blocks(const nb_ctx *c, const nb_tiles &t)
 nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req)
 {
     nb_tiles t = req;
-    const bool mixed = c->cfg.precision == NB_MIXED;
+    const bool ex = c->cfg.precision == NB_EX;
+    const bool mixed = nb_fp32_eval(c->cfg.precision);
     // defaults from the launch-shape sweep on GB300 (autotune.py): mixed
     // KI = 2 with four j per iteration; larger blocks and tiles once the
     // active set fills the grid without splitting
@@ -455,9 +568,9 @@ nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req)
     if (t.ki <= 0)
         t.ki = mixed ? 2 : 1;
     if (t.threads <= 0)
-        t.threads = mixed ? mixed_max_threads(t.ki) : 128;
+        t.threads = ex ? kExThreads : mixed ? mixed_max_threads(t.ki) : 128;
     if (t.junroll <= 0)
-        t.junroll = 4;
+        t.junroll = ex ? 2 : 4;
     if (t.lanes <= 0) {
         int l = 1;
         while (l < 32 && static_cast<int64_t>(t.threads / (2 * l)) * t.ki >= n_act)
@@ -466,13 +579,13 @@ nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req)
     }
     if (t.jtile <= 0)
         t.jtile = mixed ? (big ? 512 : 256) : 256;
-    if (mixed && t.jtile % 4)
+    if ((mixed || ex) && t.jtile % 4)
         t.jtile = (t.jtile / 4 + 1) * 4;   // whole 16-byte rows per bulk copy
     if (t.split <= 0) {
         // Split the j-range so that the grid fills whole waves of resident
         // blocks: all blocks of a launch do equal work, so a partial last
         // wave idles the rest of the GPU for a whole block's duration.
-        const int64_t jn = mixed ? c->npad : c->n;
+        const int64_t jn = (mixed || ex) ? c->npad : c->n;
         const int64_t itile = static_cast<int64_t>(t.threads / t.lanes) * t.ki;
         const int64_t nblk = (n_act + itile - 1) / itile;
         const int64_t cap = static_cast<int64_t>(c->sm_count) * resident_blocks(c, t);
@@ -504,14 +617,17 @@ cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L)
     const nb_tiles &t = L.tiles;
     if (L.n_act <= 0)
         return cudaSuccess;
-    const bool mixed = c->cfg.precision == NB_MIXED;
-    if (!(t.ki == 1 || t.ki == 2 || (t.ki == 4 && !mixed)) || t.threads < 32 ||
-        t.threads > (mixed ? mixed_max_threads(t.ki) : max_threads_for(t.ki)) || t.threads % 32 ||
-        !is_pow2(t.lanes) || t.lanes > 32 || t.jtile < 1 || t.split < 1)
+    const bool mixed = nb_fp32_eval(c->cfg.precision);
+    const bool ex = c->cfg.precision == NB_EX;
+    if (!(t.ki == 1 || (t.ki == 2 && !ex) || (t.ki == 4 && !mixed && !ex)) || t.threads < 32 ||
+        t.threads > (ex ? kExThreads : mixed ? mixed_max_threads(t.ki) : max_threads_for(t.ki)) ||
+        t.threads % 32 || !is_pow2(t.lanes) || t.lanes > 32 || t.jtile < 1 || t.split < 1)
         return cudaErrorInvalidValue;
     if (mixed && (!(t.junroll == 2 || t.junroll == 4) || t.jtile % 4))
         return cudaErrorInvalidValue;
-    const int rec = mixed ? kRecBytes32 : kRecBytes64;
+    if (ex && (!(t.junroll == 1 || t.junroll == 2) || t.jtile % 4))
+        return cudaErrorInvalidValue;
+    const int rec = ex ? kRecBytesEx : mixed ? kRecBytes32 : kRecBytes64;
     const size_t smem = static_cast<size_t>(2) * rec * t.jtile +
                         (mixed ? static_cast<size_t>(18) * t.ki * t.threads * sizeof(float) : 0);
     if (smem > 200 * 1024)
@@ -519,13 +635,13 @@ cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L)
     const int itile = (t.threads / t.lanes) * t.ki;
     const int gx = (L.n_act + itile - 1) / itile;
     // j chunk per split, a whole number of tiles
-    const int64_t jn = mixed ? c->npad : c->n;
+    const int64_t jn = (mixed || ex) ? c->npad : c->n;
     int64_t chunk = (jn + t.split - 1) / t.split;
     chunk = (chunk + t.jtile - 1) / t.jtile * t.jtile;
     const int split = static_cast<int>((jn + chunk - 1) / chunk);
 
     EvalArgs a;
-    a.jb = mixed ? static_cast<const void *>(c->jf32) : static_cast<const void *>(c->jb64);
+    a.jb = (mixed || ex) ? static_cast<const void *>(c->jf32) : static_cast<const void *>(c->jb64);
     a.n = static_cast<int>(jn);
     a.act = L.act;
     a.n_act = L.n_act;
@@ -568,7 +684,10 @@ cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L)
         a.cnt = c->tile_cnt;
     }
     const dim3 grid(gx, split), block(t.threads);
-    if (mixed) {
+    if (ex) {
+        if (t.junroll == 1) eval_ex_kernel<float><<<grid, block, smem, c->stream>>>(a);
+        else eval_ex_kernel<float2><<<grid, block, smem, c->stream>>>(a);
+    } else if (mixed) {
         if (t.ki == 1 && t.junroll == 2) eval_mixed_kernel<1, 2><<<grid, block, smem, c->stream>>>(a);
         else if (t.ki == 1) eval_mixed_kernel<1, 4><<<grid, block, smem, c->stream>>>(a);
         else if (t.junroll == 2) eval_mixed_kernel<2, 2><<<grid, block, smem, c->stream>>>(a);

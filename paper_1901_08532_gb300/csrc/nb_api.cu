@@ -1,6 +1,7 @@
 // C-ABI of libnb (declared in include/nb.h): argument checking, device
 // memory ownership, error reporting, and the order of kernel launches for
 // the predictor -> evaluation -> corrector cycle of the paper's section 3.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -58,8 +59,8 @@ bool finite_all(const double *p, int64_t n)
 
 std::string check_config(const nb_config &c)
 {
-    if (c.precision != NB_FP64 && c.precision != NB_MIXED)
-        return "precision must be NB_FP64 or NB_MIXED";
+    if (c.precision != NB_FP64 && c.precision != NB_MIXED && c.precision != NB_SP && c.precision != NB_EX)
+        return "precision must be NB_FP64, NB_MIXED, NB_SP or NB_EX";
     if (!(c.eta > 0.0) || !std::isfinite(c.eta))
         return "eta must be positive";
     if (!(c.eta_s > 0.0) || !std::isfinite(c.eta_s))
@@ -179,6 +180,7 @@ void free_all(nb_ctx *c)
     cudaFree(c->red);
     cudaFree(c->ctl);
     cudaFree(c->diag);
+    cudaFree(c->ring);
     if (c->ctl_h)
         cudaFreeHost(c->ctl_h);
     if (c->diag_h)
@@ -239,10 +241,11 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x, con
     }
     // eps^2 must be an FP32 normal number (FP64 rsqrt estimate); the mixed
     // path also needs m / eps^3 to stay below the FP32 range.
-    const double eps_min = cf.precision == NB_MIXED ? std::ldexp(1.0, -40) : std::ldexp(1.0, -60);
+    const bool fp32_range = nb_jrows(cf.precision) > 0;
+    const double eps_min = fp32_range ? std::ldexp(1.0, -40) : std::ldexp(1.0, -60);
     if (!(eps >= eps_min) || !(eps <= 1e18)) {
-        g_init_err = cf.precision == NB_MIXED ? "eps must be in [2^-40, 1e18] for NB_MIXED"
-                                              : "eps must be in [2^-60, 1e18]";
+        g_init_err = fp32_range ? "eps must be in [2^-40, 1e18] for FP32 pair arithmetic"
+                                : "eps must be in [2^-60, 1e18]";
         return NB_EINVAL;
     }
     for (int64_t i = 0; i < n; ++i)
@@ -284,9 +287,9 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x, con
     CUI(cudaMalloc(&c->t, N * sizeof(double)));
     CUI(cudaMalloc(&c->dt, N * sizeof(double)));
     c->npad = (n + 3) / 4 * 4;
-    if (cf.precision == NB_MIXED) {
-        CUI(cudaMalloc(&c->jf32, 13 * static_cast<size_t>(c->npad) * sizeof(float)));
-        CUI(cudaMemsetAsync(c->jf32, 0, 13 * static_cast<size_t>(c->npad) * sizeof(float), c->stream));
+    if (const int rows = nb_jrows(cf.precision)) {
+        CUI(cudaMalloc(&c->jf32, rows * static_cast<size_t>(c->npad) * sizeof(float)));
+        CUI(cudaMemsetAsync(c->jf32, 0, rows * static_cast<size_t>(c->npad) * sizeof(float), c->stream));
     } else
         CUI(cudaMalloc(&c->jb64, 5 * N * sizeof(double2)));
     CUI(cudaMalloc(&c->act, N * sizeof(int32_t)));
@@ -355,7 +358,20 @@ nb_status nb_get_predicted(nb_ctx *c, double *xp, double *vp, double *ap)
     if (!c->have_pred)
         return fail(c, NB_ESTATE, "nb_get_predicted needs a prediction (nb_predict) first");
     const size_t N = static_cast<size_t>(c->n);
-    if (c->cfg.precision == NB_MIXED) {
+    if (c->cfg.precision == NB_EX) {
+        const size_t P = static_cast<size_t>(c->npad);
+        std::vector<float> h(20 * P);
+        CU(c, cudaMemcpyAsync(h.data(), c->jf32, 20 * P * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CU(c, cudaStreamSynchronize(c->stream));
+        double *dst[3] = {xp, vp, ap};
+        for (size_t i = 0; i < N; ++i)
+            for (int g = 0; g < 3; ++g)
+                if (dst[g])
+                    for (int d = 0; d < 3; ++d)
+                        dst[g][3 * i + d] = (double)h[(6 * g + d) * P + i] + (double)h[(6 * g + 3 + d) * P + i];
+        return NB_OK;
+    }
+    if (nb_fp32_eval(c->cfg.precision)) {
         const size_t P = static_cast<size_t>(c->npad);
         std::vector<float> h(13 * P);
         CU(c, cudaMemcpyAsync(h.data(), c->jf32, 13 * P * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
@@ -499,6 +515,93 @@ nb_status nb_run_until(nb_ctx *c, double t_end, int64_t *steps_out, int64_t log_
     if (steps_out)
         *steps_out = steps;
     return sync_ctl(c);
+}
+
+nb_status nb_run_diag(nb_ctx *c, double t_end, double dt_diag, int64_t cap, double *out,
+                      int64_t *n_samples, int64_t *steps_out)
+{
+    CHECK_CTX(c);
+    const double quantum = c->cfg.dt_shared > 0.0 ? c->cfg.dt_shared : c->cfg.dt_max;
+    if (!std::isfinite(t_end) || !(dt_diag > 0.0) || !std::isfinite(dt_diag))
+        return fail(c, NB_EINVAL, "t_end must be finite and dt_diag > 0");
+    if (std::fmod(dt_diag, quantum) != 0.0)
+        return fail(c, NB_EINVAL, "dt_diag must be a multiple of dt_max (dt_shared in shared mode)");
+    if (std::fmod(t_end, dt_diag) != 0.0)
+        return fail(c, NB_EINVAL, "t_end must be a multiple of dt_diag");
+    if (std::fmod(c->t_sys, quantum) != 0.0)
+        return fail(c, NB_ESTATE, "the current time is not a synchronisation time");
+    if (cap < 0 || (cap > 0 && !out))
+        return fail(c, NB_EINVAL, "out must not be NULL when cap > 0");
+    if (t_end < c->t_sys)
+        return fail(c, NB_EINVAL, "t_end is before the current time");
+    const int64_t want = static_cast<int64_t>((t_end - c->t_sys) / dt_diag) + 1;
+    const int64_t keep = std::min(cap, want);
+    if (keep > c->ring_cap) {
+        cudaFree(c->ring);
+        c->ring = nullptr;
+        c->ring_cap = 0;
+        CU(c, cudaMalloc(&c->ring, static_cast<size_t>(keep) * 8 * sizeof(double)));
+        c->ring_cap = keep;
+    }
+    // Per sample: energies and angular momentum into the ring slot, the time
+    // and step count into pinned host memory (known on the host).
+    std::vector<double> hdr;
+    hdr.reserve(static_cast<size_t>(2 * keep));
+    int64_t taken = 0, steps = 0;
+    auto sample = [&](double t) -> nb_status {
+        if (taken < keep) {
+            double *slot = c->ring + 8 * taken;
+            CU(c, nb_launch_energy(c, slot + 1));
+            CU(c, nb_launch_angmom(c, slot + 3));
+            hdr.push_back(t);
+            hdr.push_back(static_cast<double>(steps));
+        }
+        ++taken;
+        return NB_OK;
+    };
+    nb_status s = sample(c->t_sys);
+    if (s != NB_OK)
+        return s;
+    double t_next = c->t_sys + dt_diag;
+    while (t_next <= t_end) {
+        for (;;) {
+            double tn;
+            int64_t na;
+            s = schedule(c, &tn, &na);
+            if (s != NB_OK)
+                return s;
+            if (tn > t_next)
+                break;
+            if (na < 1)
+                return fail(c, NB_ESTATE, "scheduler found no active particle");
+            s = advance(c, tn, na);
+            if (s != NB_OK)
+                return s;
+            c->t_sys = tn;
+            ++steps;
+        }
+        s = sample(t_next);
+        if (s != NB_OK)
+            return s;
+        t_next += dt_diag;
+    }
+    s = sync_ctl(c);
+    if (s != NB_OK)
+        return s;
+    if (keep > 0) {
+        CU(c, cudaMemcpyAsync(out, c->ring, static_cast<size_t>(keep) * 8 * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+        CU(c, cudaStreamSynchronize(c->stream));
+        for (int64_t k = 0; k < keep; ++k) {
+            out[8 * k + 0] = hdr[2 * k];
+            out[8 * k + 7] = hdr[2 * k + 1];
+        }
+    }
+    if (n_samples)
+        *n_samples = taken;
+    if (steps_out)
+        *steps_out = steps;
+    return NB_OK;
 }
 
 nb_status nb_energy(nb_ctx *c, double *ekin, double *epot)

@@ -24,6 +24,14 @@
 //   acc x,y,z, jerk x,y,z, snap x,y,z of the k-th listed particle.
 enum { F_X = 0, F_V = 1, F_A = 2, F_J = 3, F_S = 4, F_C = 5, NFIELD = 6 };
 
+// Evaluations that use the FP32 row buffer and the packed FP32 kernel.
+inline bool nb_fp32_eval(int precision) { return precision == NB_MIXED || precision == NB_SP; }
+// FP32 rows per particle of the predicted j-buffer (0: FP64 records).
+inline int nb_jrows(int precision)
+{
+    return precision == NB_EX ? 20 : (nb_fp32_eval(precision) ? 13 : 0);
+}
+
 struct nb_ctl {                      // small device control block
     unsigned long long tnext_bits;   // min over i of (t_i + dt_i), as bits
     int32_t n_act;                   // active count from the scheduler
@@ -62,6 +70,8 @@ struct nb_ctx {
     nb_ctl *ctl_h = nullptr;   // pinned host mirror
     double *diag = nullptr;    // [8] device results of energy / angmom
     double *diag_h = nullptr;  // [8] pinned host mirror
+    double *ring = nullptr;    // [ring_cap][8] diagnostics samples of nb_run_diag
+    int64_t ring_cap = 0;
 
     int64_t n_act = 0;         // size of the last evaluated set
     bool have_pred = false;

@@ -42,6 +42,11 @@ SM_MAX_MHZ = 2070.0
 # plain-ALU peaks from unit counts and the maximum SM clock
 PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
 PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12     # 1.26
+# The extended-precision (double-word) kernel issues 613 FP32-pipe operations
+# (add, sub, mul, fma) per interaction, counted from its operation sequence;
+# the FP32 pipe retires 128 of them per clock per SM.
+EX_OPS_PER_INTERACTION = 613
+PEAK_FP32_OPS = SM_COUNT * 128 * SM_MAX_MHZ * 1e6                 # 40.3e12 / s
 # DRAM traffic of one mixed evaluation launch from an ncu capture of a
 # smaller case, scaled to the full launch; valid only for the kernel source
 # it was measured on (the sha256 prefix of csrc/k_eval.cu).
@@ -70,7 +75,7 @@ def parse():
                    help="only launch the evaluation kernel --reps times on --n particles with "
                         "--n-act active (a small case for ncu captures)")
     p.add_argument("--n-act", type=int, default=4096)
-    p.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "both"])
+    p.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "both", "ex", "sp"])
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--ensemble", action="store_true",
                    help="ensemble workload: 256 Plummer systems, N log-uniform in [256, 16384] "
@@ -91,12 +96,12 @@ def parse():
                         "mode), eps 1e-3, dt 2^-10, 64 steps, checkpoints every 8; forward and "
                         "backward times")
     p.add_argument("--precision-study", action="store_true",
-                   help="energy and angular-momentum errors against time (Eq. 1) for FP64, mixed "
-                        "and single-precision positions: Plummer N=--n (default 4096 in this mode), "
+                   help="energy and angular-momentum errors against time (Eq. 1) for FP64, mixed, "
+                        "extended (double-word FP32) and single-precision positions: Plummer N=--n (default 4096 in this mode), "
                         "equal masses, eps 1e-4, block steps, a device sample every --ps-dt")
     p.add_argument("--ps-t-end", type=float, default=1.0)
     p.add_argument("--ps-dt", type=float, default=2.0 ** -3)
-    p.add_argument("--ps-precs", default="fp64,mixed,sp")
+    p.add_argument("--ps-precs", default="fp64,mixed,ex,sp")
     return p.parse_args()
 
 
@@ -378,7 +383,7 @@ def _time_eval(ctx, torch, stream, act, reps, warm=True):
 
 
 def secondary(nb, np, torch, m, x, v, st, stream, n):
-    """FP64 kernel throughput, split-j fractions, mixed error vs FP64."""
+    """FP64 and EX kernel throughput, split-j fractions, mixed and EX error vs FP64."""
     import nb_inputs as ni
     out = {}
     state = {k: st[k] for k in ("x", "v", "a", "j", "s", "c", "t", "dt")}
@@ -388,9 +393,13 @@ def secondary(nb, np, torch, m, x, v, st, stream, n):
     mixed = nb.NBody(m, x, v, EPS, precision=nb.NB_MIXED, dt_shared=2.0 ** -10, stream=stream,
                      start_forces=False)
     mixed.set_state(state)
+    ex = nb.NBody(m, x, v, EPS, precision=nb.NB_EX, dt_shared=2.0 ** -10, stream=stream,
+                  start_forces=False)
+    ex.set_state(state)
     t = 2.0 ** -10
     fp64.predict(t)
     mixed.predict(t)
+    ex.predict(t)
     fr = {}
     act_32k = ni.active_subset(n, n // 32, 32)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -411,20 +420,36 @@ def secondary(nb, np, torch, m, x, v, st, stream, n):
         fr[f"mixed_{frac}"] = {"n_act": int(act.size), "interactions_per_s": act.size * n / sm,
                                "frac_of_fp32_peak": FLOPS_PER_INTERACTION * act.size * n / sm / 1e12
                                / PEAK_FP32_TFLOPS, "tiles": mixed.resolve_tiles(act.size)}
+    at32 = torch.from_numpy(act_32k).cuda()
+    sx = _time_eval(ex, torch, stream, at32, 2)
+    rate_ex = act_32k.size * n / sx
+    fr["ex_2^-5"] = {"n_act": int(act_32k.size), "interactions_per_s": rate_ex,
+                     "fp32_ops_per_interaction": EX_OPS_PER_INTERACTION,
+                     "frac_of_fp32_pipe": EX_OPS_PER_INTERACTION * rate_ex / PEAK_FP32_OPS,
+                     "fp64_equiv_tflops": FLOPS_PER_INTERACTION * rate_ex / 1e12,
+                     "tiles": ex.resolve_tiles(act_32k.size)}
     out["fractions"] = fr
-    # mixed vs FP64 on the same predicted inputs (the 2^-5 active set)
-    am, jm, sm_ = mixed.evaluate(act_32k)
-    errs = {}
-    for name, g, r in (("acc", am, a64), ("jerk", jm, j64), ("snap", sm_, s64_)):
-        e = np.abs(g - r).max(axis=1) / np.linalg.norm(r, axis=1)
-        errs[name] = {"max": float(e.max()), "p99": float(np.percentile(e, 99)),
-                      "median": float(np.median(e)), "frac_above_1e-6": float((e > 1e-6).mean())}
+
+    def err_stats(got, ref, thr):
+        errs = {}
+        for name, g, r in zip(("acc", "jerk", "snap"), got, ref):
+            e = np.abs(g - r).max(axis=1) / np.linalg.norm(r, axis=1)
+            errs[name] = {"max": float(e.max()), "p99": float(np.percentile(e, 99)),
+                          "median": float(np.median(e)), f"frac_above_{thr:g}": float((e > thr).mean())}
+        return errs
+
+    # mixed and EX vs FP64 on the same predicted inputs (the 2^-5 active set)
+    ref = (a64, j64, s64_)
     out["mixed_vs_fp64_err"] = {"n_act": int(act_32k.size), "metric": "|d|_inf/|ref|_2 per particle",
-                                **errs}
+                                **err_stats(mixed.evaluate(act_32k), ref, 1e-6)}
+    out["ex_vs_fp64_err"] = {"n_act": int(act_32k.size), "metric": "|d|_inf/|ref|_2 per particle",
+                             **err_stats(ex.evaluate(act_32k), ref, 1e-12)}
     mixed_rate = fr["mixed_2^-5"]["interactions_per_s"]
     out["speedup_mixed_over_fp64"] = mixed_rate / fr["fp64_2^-5"]["interactions_per_s"]
+    out["speedup_ex_over_fp64"] = rate_ex / fr["fp64_2^-5"]["interactions_per_s"]
     fp64.close()
     mixed.close()
+    ex.close()
     return out
 
 
@@ -495,7 +520,7 @@ def profile_eval(args):
     stream = torch.cuda.current_stream()
     m, x, v = ni.plummer(args.n, SEED, imf="salpeter")
     a = ni.random_state(args.n, 5, scale=2.0)
-    prec = nb.NB_MIXED if args.prec == "mixed" else nb.NB_FP64
+    prec = {"mixed": nb.NB_MIXED, "fp64": nb.NB_FP64, "ex": nb.NB_EX, "sp": nb.NB_SP}[args.prec]
     ctx = nb.NBody(m, x, v, EPS, precision=prec, stream=stream, start_forces=False)
     ctx.set_state({"a": a})
     ctx.predict(0.0)
@@ -690,7 +715,7 @@ def precision_study(args):
     torch.cuda.set_device(0)
     n = args.n if args.n != N_BODY else 4096
     m, x, v = ni.plummer(n, 1)
-    precs = {"fp64": nb.NB_FP64, "mixed": nb.NB_MIXED, "sp": nb.NB_SP}
+    precs = {"fp64": nb.NB_FP64, "mixed": nb.NB_MIXED, "ex": nb.NB_EX, "sp": nb.NB_SP}
     res = {"workload": f"precision_study_plummer_N{n}_equal_eps1e-4_t{args.ps_t_end:g}",
            "sample_dt": args.ps_dt, "t_end": args.ps_t_end}
     for name in args.ps_precs.split(","):

@@ -20,6 +20,7 @@ import os
 
 MIXED_SPACE = {"ki": (1, 2), "junroll": (2, 4), "threads": (64, 128, 256), "jtile": (256, 512)}
 FP64_SPACE = {"ki": (1, 2), "threads": (64, 128, 256), "jtile": (128, 256)}
+EX_SPACE = {"ki": (1,), "junroll": (1, 2), "threads": (64, 128), "jtile": (256, 512, 1024)}
 
 _cache: dict = {}
 
@@ -29,7 +30,7 @@ def _bucket(n_act: int) -> int:
 
 
 def candidates(precision: int):
-    space = MIXED_SPACE if precision in (1, 2) else FP64_SPACE
+    space = MIXED_SPACE if precision in (1, 2) else EX_SPACE if precision == 3 else FP64_SPACE
     keys = sorted(space)
     for vals in itertools.product(*(space[k] for k in keys)):
         shape = dict(zip(keys, vals))
@@ -101,7 +102,7 @@ def main():
     p = argparse.ArgumentParser()
     p.add_argument("--n", type=int, default=1 << 20)
     p.add_argument("--n-act", type=int, nargs="+", default=[1024])
-    p.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--prec", choices=["mixed", "fp64", "ex", "sp"], default="mixed")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--seed", type=int, default=3)
     args = p.parse_args()
@@ -111,7 +112,7 @@ def main():
     import paper_1901_08532_gb300 as nb
     torch.cuda.set_device(0)
     m, x, v = ni.plummer(args.n, args.seed, imf="salpeter")
-    prec = nb.NB_MIXED if args.prec == "mixed" else nb.NB_FP64
+    prec = {"mixed": nb.NB_MIXED, "fp64": nb.NB_FP64, "ex": nb.NB_EX, "sp": nb.NB_SP}[args.prec]
     ctx = nb.NBody(m, x, v, 1e-4, precision=prec, start_forces=False)
     ctx.set_state({"a": ni.random_state(args.n, 5, scale=2.0)})
     ctx.predict(0.0)

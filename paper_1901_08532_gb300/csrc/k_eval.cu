@@ -578,7 +578,7 @@ nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req)
         t.lanes = l;
     }
     if (t.jtile <= 0)
-        t.jtile = mixed ? (big ? 512 : 256) : 256;
+        t.jtile = mixed ? (big ? 512 : 256) : (ex ? 512 : 256);
     if ((mixed || ex) && t.jtile % 4)
         t.jtile = (t.jtile / 4 + 1) * 4;   // whole 16-byte rows per bulk copy
     if (t.split <= 0) {

@@ -87,8 +87,8 @@ std::string check_tiles(const nb_tiles &t)
         return "tiles.jtile must be in [0, 4096]";
     if (t.split < 0 || t.split > 4096)
         return "tiles.split must be in [0, 4096]";
-    if (t.junroll != 0 && t.junroll != 2 && t.junroll != 4)
-        return "tiles.junroll must be 0, 2 or 4";
+    if (t.junroll != 0 && t.junroll != 1 && t.junroll != 2 && t.junroll != 4)
+        return "tiles.junroll must be 0, 1, 2 or 4";
     return "";
 }
 

@@ -254,6 +254,22 @@ def _kernel_sha():
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
+def aggregate_ranks(elapsed, interactions, device="cpu"):
+    """Whole-job figures over the ranks of an initialised process group: the
+    slowest rank's elapsed time and the sum of the interactions every rank
+    evaluated (each rank runs an independent replica).  Without a group (or
+    with one rank) the local figures are returned."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(elapsed), float(interactions)
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    k = torch.tensor([float(interactions)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(k, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(k.item())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -313,11 +329,7 @@ def run_ours(args):
         elapsed = time.perf_counter() - t0
     launches1, inter1 = mixed.counters()
     eval_ms = [a.elapsed_time(b) for a, b in evs]
-    if world > 1:
-        tt = torch.tensor([elapsed], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(tt.item())
-    interactions = (inter1 - inter0) * world
+    elapsed, interactions = aggregate_ranks(elapsed, inter1 - inter0, "cuda")
     value = interactions / elapsed
     eval_s = sum(eval_ms) / len(eval_ms) / 1e3
     achieved = FLOPS_PER_INTERACTION * float(n) * n / eval_s / 1e12
@@ -420,6 +432,14 @@ def secondary(nb, np, torch, m, x, v, st, stream, n):
         fr[f"mixed_{frac}"] = {"n_act": int(act.size), "interactions_per_s": act.size * n / sm,
                                "frac_of_fp32_peak": FLOPS_PER_INTERACTION * act.size * n / sm / 1e12
                                / PEAK_FP32_TFLOPS, "tiles": mixed.resolve_tiles(act.size)}
+    # the realistic, core-concentrated active set: the n particles with the
+    # smallest starting steps (ties by index), in ascending index order
+    core = np.sort(np.argsort(st["dt"], kind="stable")[: n // 32]).astype(np.int32)
+    sm = _time_eval(mixed, torch, stream, torch.from_numpy(core).cuda(), 5)
+    fr["mixed_core_2^-5"] = {"n_act": int(core.size), "interactions_per_s": core.size * n / sm,
+                             "frac_of_fp32_peak": FLOPS_PER_INTERACTION * core.size * n / sm / 1e12
+                             / PEAK_FP32_TFLOPS, "active_set": "smallest starting dt",
+                             "tiles": mixed.resolve_tiles(core.size)}
     at32 = torch.from_numpy(act_32k).cuda()
     sx = _time_eval(ex, torch, stream, at32, 2)
     rate_ex = act_32k.size * n / sx

@@ -9,10 +9,11 @@
 //   Fast2Sum (Dekker):      s + e == a + b exactly when |a| >= |b| (or a == 0);
 //   TwoProd (FMA form):     p + e == a * b exactly (barring underflow),
 //                           e = fma(a, b, -p);
-// and on top of them the "sloppy" double-word sum and the double-word
-// product of Dekker (1971), whose error bounds are analysed by Joldes,
-// Muller and Popescu (ACM TOMS 44, 2017): relative error of a product
-// <= about 4 u^2, of a sum <= about 2 u^2 (|x| + |y|) / |x + y|, u = 2^-24.
+// and on top of them the "sloppy" and accurate double-word sums and the
+// double-word product of Dekker (1971), whose error bounds are analysed by
+// Joldes, Muller and Popescu (ACM TOMS 44, 2017): relative error of a
+// product <= about 4 u^2, of a sloppy sum <= about 2 u^2 (|x| + |y|) /
+// |x + y|, of an accurate sum <= about 3 u^2, u = 2^-24.
 //
 // Every helper is written for T = float (one value) or T = float2 (two
 // independent values in the lanes of the packed f32x2 instructions).  The
@@ -67,16 +68,24 @@ __device__ __forceinline__ FF<T> two_prod(T a, T b)
     return {p, fma(a, b, neg(p))};
 }
 
-// x + y, normalised (the "sloppy" double-word sum: exact for the high
-// parts, the low parts added in FP32; accurate unless x and y nearly cancel).
+// The operations below return UNNORMALISED double words: the high part is
+// the FP32 rounding of the leading term and the low part gathers everything
+// else, so |l| may exceed ulp(h)/2 by a few ulps.  Skipping the final
+// Fast2Sum of the textbook forms saves three operations per call and does
+// not change the value h + l; the products and sums that consume such a
+// pair stay accurate to a few u^2 of their operands (a float32 emulation of
+// the pair term below gives the same errors with and without it).
+
+// x + y, the "sloppy" double-word sum: exact for the high parts, the low
+// parts added in FP32; accurate unless x and y nearly cancel.
 template <class T>
 __device__ __forceinline__ FF<T> add(const FF<T> &x, const FF<T> &y)
 {
     const FF<T> s = two_sum(x.h, y.h);
-    return fast_two_sum(s.h, add(s.l, add(x.l, y.l)));
+    return {s.h, add(s.l, add(x.l, y.l))};
 }
 
-// x + y with relative error below 3 u^2 even under cancellation (the
+// x + y with relative error of a few u^2 even under cancellation (the
 // accurate double-word sum: both parts pass through TwoSum).
 template <class T>
 __device__ __forceinline__ FF<T> add_accurate(const FF<T> &x, const FF<T> &y)
@@ -84,10 +93,10 @@ __device__ __forceinline__ FF<T> add_accurate(const FF<T> &x, const FF<T> &y)
     const FF<T> s = two_sum(x.h, y.h);
     const FF<T> t = two_sum(x.l, y.l);
     const FF<T> v = fast_two_sum(s.h, add(s.l, t.h));
-    return fast_two_sum(v.h, add(t.l, v.l));
+    return {v.h, add(t.l, v.l)};
 }
 
-// x * y, normalised (the l * l term is below the format's resolution).
+// x * y (the l * l term is below the format's resolution).
 template <class T>
 __device__ __forceinline__ FF<T> mul(const FF<T> &x, const FF<T> &y)
 {
@@ -95,7 +104,7 @@ __device__ __forceinline__ FF<T> mul(const FF<T> &x, const FF<T> &y)
     T e = fma(x.h, y.h, neg(p));
     e = fma(x.h, y.l, e);
     e = fma(x.l, y.h, e);
-    return fast_two_sum(p, e);
+    return {p, e};
 }
 
 // x * c for an FP32 constant c.
@@ -103,21 +112,19 @@ template <class T>
 __device__ __forceinline__ FF<T> mul(const FF<T> &x, T c)
 {
     const T p = mul(x.h, c);
-    const T e = fma(x.l, c, fma(x.h, c, neg(p)));
-    return fast_two_sum(p, e);
+    return {p, fma(x.l, c, fma(x.h, c, neg(p)))};
 }
 
-// x * x, normalised.
+// x * x.
 template <class T>
 __device__ __forceinline__ FF<T> sqr(const FF<T> &x)
 {
     const T p = mul(x.h, x.h);
-    const T e = fma(add(x.h, x.h), x.l, fma(x.h, x.h, neg(p)));
-    return fast_two_sum(p, e);
+    return {p, fma(add(x.h, x.h), x.l, fma(x.h, x.h, neg(p)))};
 }
 
 // x * y + z in one pass: the exact product's high part meets z.h in a
-// TwoSum and all lower-order terms are gathered before one normalisation.
+// TwoSum and all lower-order terms are gathered in the low part.
 template <class T>
 __device__ __forceinline__ FF<T> mad(const FF<T> &x, const FF<T> &y, const FF<T> &z)
 {
@@ -126,7 +133,7 @@ __device__ __forceinline__ FF<T> mad(const FF<T> &x, const FF<T> &y, const FF<T>
     e = fma(x.h, y.l, e);
     e = fma(x.l, y.h, e);
     const FF<T> s = two_sum(p, z.h);
-    return fast_two_sum(s.h, add(s.l, add(e, z.l)));
+    return {s.h, add(s.l, add(e, z.l))};
 }
 
 // R^(-1/2) for R > 0: the special-function estimate q0 (relative error
@@ -155,16 +162,11 @@ __device__ __forceinline__ void accumulate(FF<T> &acc, const FF<T> &t)
     acc.l = add(acc.l, add(s.l, t.l));
 }
 
-// acc += x * y, the product left unnormalised (its low part goes straight
-// into acc.l).
+// acc += x * y (the product's low part goes straight into acc.l).
 template <class T>
 __device__ __forceinline__ void accumulate_mul(FF<T> &acc, const FF<T> &x, const FF<T> &y)
 {
-    const T p = mul(x.h, y.h);
-    T e = fma(x.h, y.h, neg(p));
-    e = fma(x.h, y.l, e);
-    e = fma(x.l, y.h, e);
-    accumulate(acc, FF<T>{p, e});
+    accumulate(acc, mul(x, y));
 }
 
 }  // namespace ff

@@ -47,10 +47,10 @@ PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12     # 1.26
 # the FP32 pipe retires 128 of them per clock per SM.
 EX_OPS_PER_INTERACTION = 613
 PEAK_FP32_OPS = SM_COUNT * 128 * SM_MAX_MHZ * 1e6                 # 40.3e12 / s
-# DRAM traffic of one mixed evaluation launch from an ncu capture of a
-# smaller case, scaled to the full launch; valid only for the kernel source
-# it was measured on (the sha256 prefix of csrc/k_eval.cu).
-TRAFFIC = {"kernel_sha": "2bf5d42ec5a41ca4", "bytes_per_launch": 118.36e6 + 69.43e6,
+# DRAM traffic of one mixed evaluation launch (the bench's own launch, one
+# ncu pass); valid only for the kernel source it was measured on (the sha256
+# prefix of csrc/k_eval.cu and csrc/nb_device.cuh).
+TRAFFIC = {"kernel_sha": "f48d47d3a8d9b0db", "bytes_per_launch": 119.15e6 + 69.61e6,
            "source": "profiles/eval_mixed_dram_plummer_N1048576_all_active.md"}
 WORKLOAD = "plummer_salpeter_N1048576_eps1e-4_shared_step_all_active"
 
@@ -82,7 +82,7 @@ def parse():
                         "(seed 4), each to --ens-t-end; one persistent launch vs one at a time")
     p.add_argument("--ens-t-end", type=float, default=0.25)
     p.add_argument("--ens-systems", type=int, default=256)
-    p.add_argument("--ens-shapes", default="4x256",
+    p.add_argument("--ens-shapes", default="4x128",
                    help="comma-separated ctas_per_system x threads [x jtile] shapes to time")
     p.add_argument("--ens-sample", type=int, default=8,
                    help="systems in the one-at-a-time comparison (0: skip)")
@@ -250,8 +250,11 @@ class Clocks:
 
 
 def _kernel_sha():
-    with open(os.path.join(ROOT, "paper_1901_08532_gb300", "csrc", "k_eval.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("k_eval.cu", "nb_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1901_08532_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def aggregate_ranks(elapsed, interactions, device="cpu"):

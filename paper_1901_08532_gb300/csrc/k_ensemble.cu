@@ -50,7 +50,7 @@ struct nb_ensemble {
     int64_t *steps = nullptr;
     unsigned long long *inter = nullptr;
     nb_ctl *ctl = nullptr, *ctl_h = nullptr;
-    int G = 8, threads = 256, jtile = 256;
+    int G = 4, threads = 128, jtile = 256;   // defaults: fastest shape of a sweep on GB300
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     double graph_t_end = -1.0;

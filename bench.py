@@ -42,10 +42,11 @@ SM_MAX_MHZ = 2070.0
 # plain-ALU peaks from unit counts and the maximum SM clock
 PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
 PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12     # 1.26
-# The extended-precision (double-word) kernel issues 613 FP32-pipe operations
-# (add, sub, mul, fma) per interaction, counted from its operation sequence;
-# the FP32 pipe retires 128 of them per clock per SM.
-EX_OPS_PER_INTERACTION = 613
+# The extended-precision (double-word) kernel issues 496 FP32-pipe operations
+# (add, sub, mul, fma; sign flips not counted) per interaction, counted from
+# the operation sequence of its pair term; the FP32 pipe retires 128 of them
+# per clock per SM.
+EX_OPS_PER_INTERACTION = 496
 PEAK_FP32_OPS = SM_COUNT * 128 * SM_MAX_MHZ * 1e6                 # 40.3e12 / s
 # DRAM traffic of one mixed evaluation launch (the bench's own launch, one
 # ncu pass); valid only for the kernel source it was measured on (the sha256

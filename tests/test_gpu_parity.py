@@ -215,19 +215,29 @@ def test_kepler_shared_steps_follow_analytic_orbit():
     assert np.abs(st["x"] - ref.state()["x"]).max() < 1e-13
 
 
+@pytest.mark.parametrize("prec", [0, 1, 3])
 @pytest.mark.parametrize("n", [1, 2, 3, 31, 33])
-def test_tiny_systems(n):
+def test_tiny_systems(n, prec):
+    """Sizes below one j-tile and one warp, in FP64, mixed and EX; the step
+    decisions must match the oracle's (a, j, s differ only by rounding)."""
     nb = nb_gpu()
     m, x, v = ni.plummer(max(n, 1), 12)
     if n == 1:
         x = np.zeros((1, 3)) + 0.3
         v = np.zeros((1, 3))
         m = np.ones(1)
-    g = nb.NBody(m, x, v, 1e-3)
+    g = nb.NBody(m, x, v, 1e-3, precision=prec)
     ref = O.System(m, x, v, 1e-3)
     st_g, st_r = g.state(), ref.state()
+    rtol = {0: 1e-12, 1: 1e-5, 3: 1e-10}[prec]
     for k in ("a", "j", "s"):
-        np.testing.assert_allclose(st_g[k], st_r[k], rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(st_g[k], st_r[k], rtol=rtol, atol=1e-300)
+    if prec == 1 and not np.array_equal(st_g["dt"], st_r["dt"]):
+        # FP32 rounding moved a starting step across a power of two: another
+        # valid trajectory; the steps may differ by one factor of two only
+        assert set(np.unique(st_g["dt"] / st_r["dt"])) <= {0.5, 1.0, 2.0}
+        g.close()
+        return
     np.testing.assert_array_equal(st_g["dt"], st_r["dt"])
     t_r, n_r, _ = ref.step()
     t_g, n_g = g.step()

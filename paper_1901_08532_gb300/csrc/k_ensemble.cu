@@ -7,12 +7,16 @@
 // the next system from an atomic queue (largest systems first) and runs its
 // whole block-step loop to t_end:
 //   schedule  t_next = min(t_i + dt_i) over the system; active set in
-//             ascending order (each CTA scans its slice, sums across the
-//             cluster through distributed shared memory);
+//             ascending order (each CTA scans its slice once, the minima and
+//             counts meet through distributed shared memory);
 //   predict   each CTA its slice, into the system's evaluation buffer;
-//   evaluate  each CTA a share of the active particles against all of the
-//             system's particles, j-tiles by TMA bulk copy into shared memory;
-//   correct   each CTA the particles it evaluated.
+//   evaluate  small active sets (<= kSmall): every CTA evaluates the whole
+//             set against its own slice and the owner of each active
+//             particle adds the CTAs' partial sums in rank order (two cluster
+//             barriers per block step); larger sets: each CTA a share of the
+//             active particles against all of the system's particles, j-tiles
+//             by TMA bulk copy into shared memory;
+//   correct   the owner (small sets) or the evaluating CTA (larger sets).
 // Phases are separated by the cluster barrier (a hardware barrier with
 // release/acquire semantics at cluster scope, no flag spinning).  Systems are
 // independent, so no grid-wide synchronisation exists.  The only waits that
@@ -45,6 +49,7 @@ struct nb_ensemble {
     double *m = nullptr, *st = nullptr, *t = nullptr, *dt = nullptr, *anew = nullptr;
     double2 *jb64 = nullptr;
     float *jf32 = nullptr;
+    float *st32 = nullptr;  // mixed: FP32 copy of the state [24][P] (rows: see predict_one_mixed)
     int32_t *act = nullptr;
     int *queue = nullptr;
     int64_t *steps = nullptr;
@@ -71,6 +76,7 @@ struct EnsArgs {
     const double *m;
     double2 *jb64;
     float *jf32;
+    float *st32;
     int32_t *act;
     double *anew;
     int *queue;
@@ -99,22 +105,6 @@ __device__ __forceinline__ double block_min(double v, double *red)
     return r;
 }
 
-// Ordered compaction of the due particles of [lo, hi): each thread takes a
-// contiguous chunk, so a block-wide exclusive scan keeps index order.
-__device__ int count_due(const EnsArgs &a, int lo, int hi, double tn, int &mine, int &first)
-{
-    const int T = blockDim.x;
-    const int len = hi - lo;
-    const int per = (len + T - 1) / T;
-    first = lo + threadIdx.x * per;
-    const int last = min(hi, first + per);
-    int c = 0;
-    for (int i = first; i < last; ++i)
-        c += (a.t[i] + a.dt[i] == tn) ? 1 : 0;
-    mine = c;
-    return c;
-}
-
 __device__ int block_exclusive_scan(int v, int *red, int *total)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -138,29 +128,91 @@ __device__ int block_exclusive_scan(int v, int *red, int *total)
     return base + incl - v;
 }
 
+// Taylor prediction of particle i to tp (FP64, through crackle).
+__device__ __forceinline__ void predict_one(const EnsArgs &a, int i, double tp, Taylor (&p)[3])
+{
+    const size_t P = static_cast<size_t>(a.P);
+    const double d = tp - a.t[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        p[k] = taylor(a.st[(F_X * 3 + k) * P + i], a.st[(F_V * 3 + k) * P + i], a.st[(F_A * 3 + k) * P + i],
+                      a.st[(F_J * 3 + k) * P + i], a.st[(F_S * 3 + k) * P + i], a.st[(F_C * 3 + k) * P + i], d);
+}
+
+// The record the mixed evaluation reads (x_hi, x_lo, v, a in FP32) predicted
+// to tp from an FP32 copy of the state: rows 0-2 v_hi, 3-5 a, 6-8 jerk,
+// 9-11 snap, 12-14 crackle, 15-17 x_hi, 18-20 x_lo, 21-23 v_lo (x and v as
+// double words, hi + lo of the FP64 values).  The predicted v and a are
+// Horner sums in FP32; x = x0 + d (v0 + d/2 I) with
+// I = a0 + d/3 (j0 + d/4 (s0 + d/5 c0)) is formed in double-word
+// arithmetic: d v_hi exactly by TwoProd (d = tp - t_i is a dyadic step of at
+// most 18 significant bits, exact in FP32), the smaller terms in FP32, then
+// TwoSum with x and one renormalisation.  x then carries about 2^-47 |x|
+// plus the FP32 rounding of its acceleration term, about 1e-7 of d^2 |a| / 2,
+// below the FP32 rounding the pair arithmetic applies to the differences.
+struct MixedRec {
+    float xh[3], xl[3], v[3], a[3];
+};
+
+constexpr int kSt32Rows = 24;
+
+__device__ __forceinline__ void predict_one_mixed(const EnsArgs &a, int i, double tp, MixedRec &r)
+{
+    const size_t P = static_cast<size_t>(a.P);
+    const float df = __double2float_rn(tp - a.t[i]);
+    const float d2 = df * 0.5f, d3 = df * (1.0f / 3.0f), d4 = df * 0.25f, d5 = df * 0.2f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float vh = a.st32[k * P + i], ac = a.st32[(3 + k) * P + i], j = a.st32[(6 + k) * P + i];
+        const float sn = a.st32[(9 + k) * P + i], c = a.st32[(12 + k) * P + i];
+        const float xh = a.st32[(15 + k) * P + i], xl = a.st32[(18 + k) * P + i];
+        const float vl = a.st32[(21 + k) * P + i];
+        r.a[k] = fmaf(df, fmaf(d2, fmaf(d3, c, sn), j), ac);
+        r.v[k] = __fadd_rn(fmaf(df, fmaf(d2, fmaf(d3, fmaf(d4, c, sn), j), ac), vh), vl);
+        const float I = fmaf(d3, fmaf(d4, fmaf(d5, c, sn), j), ac);
+        const float p = __fmul_rn(df, vh);
+        const float e = fmaf(df, fmaf(d2, I, vl), fmaf(df, vh, -p));
+        // TwoSum(xh, p), low parts gathered, renormalised
+        const float s = __fadd_rn(xh, p);
+        const float bp = __fsub_rn(s, xh);
+        const float t = __fadd_rn(__fadd_rn(__fsub_rn(xh, __fsub_rn(s, bp)), __fsub_rn(p, bp)),
+                                  __fadd_rn(xl, e));
+        const float h = __fadd_rn(s, t);
+        r.xh[k] = h;
+        r.xl[k] = __fsub_rn(t, __fsub_rn(h, s));
+    }
+}
+
+// Write the FP32 copy of a particle's x and v (double words) from FP64.
+__device__ __forceinline__ void store_xv32(const EnsArgs &a, int i, int k, double x, double v)
+{
+    const size_t P = static_cast<size_t>(a.P);
+    const float xh = __double2float_rn(x), vh = __double2float_rn(v);
+    a.st32[(15 + k) * P + i] = xh;
+    a.st32[(18 + k) * P + i] = __double2float_rn(x - static_cast<double>(xh));
+    a.st32[k * P + i] = vh;
+    a.st32[(21 + k) * P + i] = __double2float_rn(v - static_cast<double>(vh));
+}
+
 template <bool MIXED>
 __device__ void predict_slice(const EnsArgs &a, int lo, int hi, double tp)
 {
     const size_t P = static_cast<size_t>(a.P);
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const double d = tp - a.t[i];
-        Taylor p[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            p[k] = taylor(a.st[(F_X * 3 + k) * P + i], a.st[(F_V * 3 + k) * P + i],
-                          a.st[(F_A * 3 + k) * P + i], a.st[(F_J * 3 + k) * P + i],
-                          a.st[(F_S * 3 + k) * P + i], a.st[(F_C * 3 + k) * P + i], d);
         if (MIXED) {
+            MixedRec r;
+            predict_one_mixed(a, i, tp, r);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const float h = __double2float_rn(p[k].x);
-                a.jf32[k * P + i] = h;
-                a.jf32[(4 + k) * P + i] = __double2float_rn(p[k].x - static_cast<double>(h));
-                a.jf32[(7 + k) * P + i] = __double2float_rn(p[k].v);
-                a.jf32[(10 + k) * P + i] = __double2float_rn(p[k].a);
+                a.jf32[k * P + i] = r.xh[k];
+                a.jf32[(4 + k) * P + i] = r.xl[k];
+                a.jf32[(7 + k) * P + i] = r.v[k];
+                a.jf32[(10 + k) * P + i] = r.a[k];
             }
             a.jf32[3 * P + i] = __double2float_rn(a.m[i]);
         } else {
+            Taylor p[3];
+            predict_one(a, i, tp, p);
             a.jb64[i] = make_double2(p[0].x, p[1].x);
             a.jb64[P + i] = make_double2(p[2].x, a.m[i]);
             a.jb64[2 * P + i] = make_double2(p[0].v, p[1].v);
@@ -310,48 +362,252 @@ __device__ bool eval_share(const EnsArgs &a, int off, int nj, int s0, int s1, un
     return true;
 }
 
-// Corrector, interpolation and new step for slots [s0, s1) at time tn.
+// Corrector, interpolation and new step of particle i at time tn, with its
+// new acceleration, jerk and snap f[0..8].
+__device__ void correct_one(const EnsArgs &a, int i, double tn, const double (&f)[9])
+{
+    const size_t P = static_cast<size_t>(a.P);
+    const double h = tn - a.t[i];
+    const double ih = 1.0 / h;
+    double n2[6] = {0, 0, 0, 0, 0, 0};
+    bool finite = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double *px = a.st + (F_X * 3 + d) * P + i, *pv = a.st + (F_V * 3 + d) * P + i;
+        double *pa = a.st + (F_A * 3 + d) * P + i, *pj = a.st + (F_J * 3 + d) * P + i;
+        double *ps = a.st + (F_S * 3 + d) * P + i, *pc = a.st + (F_C * 3 + d) * P + i;
+        const double a1 = f[d], j1 = f[3 + d], s1v = f[6 + d];
+        const Corrected r = hermite_correct(h, ih, *px, *pv, *pa, *pj, *ps, a1, j1, s1v);
+        finite = finite && isfinite(r.x1) && isfinite(r.v1) && isfinite(r.c1);
+        *px = r.x1;
+        *pv = r.v1;
+        *pa = a1;
+        *pj = j1;
+        *ps = s1v;
+        *pc = r.c1;
+        if (a.st32) {
+            store_xv32(a, i, d, r.x1, r.v1);
+            a.st32[(3 + d) * P + i] = __double2float_rn(a1);
+            a.st32[(6 + d) * P + i] = __double2float_rn(j1);
+            a.st32[(9 + d) * P + i] = __double2float_rn(s1v);
+            a.st32[(12 + d) * P + i] = __double2float_rn(r.c1);
+        }
+        n2[0] = fma(a1, a1, n2[0]);
+        n2[1] = fma(j1, j1, n2[1]);
+        n2[2] = fma(s1v, s1v, n2[2]);
+        n2[3] = fma(r.c1, r.c1, n2[3]);
+        n2[4] = fma(r.d1, r.d1, n2[4]);
+        n2[5] = fma(r.e1, r.e1, n2[5]);
+    }
+    a.t[i] = tn;
+    bool hit = false;
+    a.dt[i] = a.dt_shared > 0.0 ? a.dt_shared
+                                : quantise(aarseth_dt(n2, a.eta), a.dt[i], tn, a.dt_min, a.dt_max, &hit);
+    if (hit)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->floor_hits), 1ull);
+    if (!finite)
+        atomicOr(&a.ctl->err, NB_ERR_NONFINITE);
+}
+
+// Corrector for active slots [s0, s1) at time tn (new values in anew).
 __device__ void correct_share(const EnsArgs &a, int off, int s0, int s1, double tn)
 {
     const size_t P = static_cast<size_t>(a.P);
     for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
-        const int i = a.act[off + k];
-        const double h = tn - a.t[i];
-        const double ih = 1.0 / h;
-        double n2[6] = {0, 0, 0, 0, 0, 0};
-        bool finite = true;
+        double f[9];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            double *px = a.st + (F_X * 3 + d) * P + i, *pv = a.st + (F_V * 3 + d) * P + i;
-            double *pa = a.st + (F_A * 3 + d) * P + i, *pj = a.st + (F_J * 3 + d) * P + i;
-            double *ps = a.st + (F_S * 3 + d) * P + i, *pc = a.st + (F_C * 3 + d) * P + i;
-            const double a1 = a.anew[(0 + d) * P + off + k];
-            const double j1 = a.anew[(3 + d) * P + off + k];
-            const double s1v = a.anew[(6 + d) * P + off + k];
-            const Corrected r = hermite_correct(h, ih, *px, *pv, *pa, *pj, *ps, a1, j1, s1v);
-            finite = finite && isfinite(r.x1) && isfinite(r.v1) && isfinite(r.c1);
-            *px = r.x1;
-            *pv = r.v1;
-            *pa = a1;
-            *pj = j1;
-            *ps = s1v;
-            *pc = r.c1;
-            n2[0] = fma(a1, a1, n2[0]);
-            n2[1] = fma(j1, j1, n2[1]);
-            n2[2] = fma(s1v, s1v, n2[2]);
-            n2[3] = fma(r.c1, r.c1, n2[3]);
-            n2[4] = fma(r.d1, r.d1, n2[4]);
-            n2[5] = fma(r.e1, r.e1, n2[5]);
-        }
-        a.t[i] = tn;
-        bool hit = false;
-        a.dt[i] = a.dt_shared > 0.0 ? a.dt_shared
-                                    : quantise(aarseth_dt(n2, a.eta), a.dt[i], tn, a.dt_min, a.dt_max, &hit);
-        if (hit)
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->floor_hits), 1ull);
-        if (!finite)
-            atomicOr(&a.ctl->err, NB_ERR_NONFINITE);
+        for (int q = 0; q < 9; ++q)
+            f[q] = a.anew[q * P + off + k];
+        correct_one(a, a.act[off + k], tn, f);
     }
+}
+
+// Small active sets (at most kSmall particles, the usual case once close
+// pairs sit at small steps): every block evaluates the whole active set
+// against its own slice of the system, just predicted by itself, and leaves
+// 9 partial sums per active particle in shared memory; the block that owns
+// a particle adds the cluster's partials in rank order and corrects it.
+constexpr int kSmall = 16;
+
+// i-values of the small active set: FP64 x, v, a; in mixed precision the
+// same slots hold 12 negated FP32 values (x_hi, x_lo, v, a) of the record the
+// predictor writes for particle i.
+template <bool MIXED>
+__device__ __forceinline__ void store_ivalues(const EnsArgs &a, int i, double tn, double *iv)
+{
+    if (MIXED) {
+        MixedRec r;
+        predict_one_mixed(a, i, tn, r);
+        float *f = reinterpret_cast<float *>(iv);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            f[k] = -r.xh[k];
+            f[3 + k] = -r.xl[k];
+            f[6 + k] = -r.v[k];
+            f[9 + k] = -r.a[k];
+        }
+    } else {
+        Taylor p[3];
+        predict_one(a, i, tn, p);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            iv[k] = p[k].x;
+            iv[3 + k] = p[k].v;
+            iv[6 + k] = p[k].a;
+        }
+    }
+}
+
+// Partial sums of the K active particles (i-values in iv) over the j of
+// [lo, hi), written to part[K][9].  The j are predicted to tn chunk by chunk
+// straight into shared memory (cap records per chunk, the layout of the
+// evaluation buffer: 13 FP32 rows, or 5 rows of double2), so the sums read
+// on-chip data only.  L = T / K2 lanes per active particle (K2 the power of
+// two >= K); lanes take every L-th j (pair of j in mixed precision) and are
+// combined in a fixed order.
+template <bool MIXED>
+__device__ void eval_small(const EnsArgs &a, int lo, int hi, double tn, int K, const double (*iv)[9],
+                           double (*part)[9], double (*wred)[9], unsigned char *smem, int cap)
+{
+    const int T = blockDim.x, tid = threadIdx.x;
+    int K2 = 1;
+    while (K2 < K)
+        K2 <<= 1;
+    const int L = T / K2;
+    const int g = tid / L, lane = tid - g * L;
+    const bool valid = g < K;
+    const int gi = valid ? g : 0;
+    double acc[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+        acc[q] = 0.0;
+    float2 ni[12];
+    float2 pt[9];
+    float ah[9], al[9];  // mixed: compensated (hi, lo) running sums
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+        ah[q] = al[q] = 0.0f;
+    int cnt = 0;
+    if (MIXED) {
+        const float *ivf = reinterpret_cast<const float *>(iv[gi]);
+#pragma unroll
+        for (int q = 0; q < 12; ++q)
+            ni[q] = f2(ivf[q]);
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            pt[q] = f2(0.0f);
+    }
+    const float2 eps2f = f2(static_cast<float>(a.eps2));
+    float *sf = reinterpret_cast<float *>(smem);
+    double2 *sd = reinterpret_cast<double2 *>(smem);
+    for (int b = lo; b < hi; b += cap) {
+        const int len = min(cap, hi - b);
+        for (int u = tid; u < len; u += T) {
+            const double mj = a.m[b + u];
+            if (MIXED) {
+                MixedRec r;
+                predict_one_mixed(a, b + u, tn, r);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    sf[k * cap + u] = r.xh[k];
+                    sf[(4 + k) * cap + u] = r.xl[k];
+                    sf[(7 + k) * cap + u] = r.v[k];
+                    sf[(10 + k) * cap + u] = r.a[k];
+                }
+                sf[3 * cap + u] = __double2float_rn(mj);
+            } else {
+                Taylor p[3];
+                predict_one(a, b + u, tn, p);
+                sd[u] = make_double2(p[0].x, p[1].x);
+                sd[cap + u] = make_double2(p[2].x, mj);
+                sd[2 * cap + u] = make_double2(p[0].v, p[1].v);
+                sd[3 * cap + u] = make_double2(p[2].v, p[0].a);
+                sd[4 * cap + u] = make_double2(p[1].a, p[2].a);
+            }
+        }
+        __syncthreads();
+        if (MIXED) {
+            for (int jj = 2 * lane; jj < len; jj += 2 * L) {
+                float2 c[NCF];
+                if (jj + 1 < len) {
+#pragma unroll
+                    for (int r = 0; r < NCF; ++r)
+                        c[r] = *reinterpret_cast<const float2 *>(sf + r * cap + jj);
+                } else {
+                    // odd tail: the second half repeats the first j with no mass
+#pragma unroll
+                    for (int r = 0; r < NCF; ++r) {
+                        const float x0 = sf[r * cap + jj];
+                        c[r] = make_float2(x0, r == 3 ? 0.0f : x0);
+                    }
+                }
+                pair_mixed2(c, ni, eps2f, pt);
+                if (++cnt == 32) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        two_sum_acc(ah[q], al[q], __fadd_rn(pt[q].x, pt[q].y));
+                        pt[q] = f2(0.0f);
+                    }
+                    cnt = 0;
+                }
+            }
+        } else {
+            const double *v = iv[gi];
+            for (int jj = lane; jj < len; jj += L)
+                pair_fp64(sd[jj], sd[cap + jj], sd[2 * cap + jj], sd[3 * cap + jj], sd[4 * cap + jj], v[0],
+                          v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8], a.eps2, acc);
+        }
+        __syncthreads();
+    }
+    const int w = tid >> 5;
+    const int span = L < 32 ? L : 32;  // lanes combined by shuffles
+    if (MIXED) {
+        // fixed-order double-word sums across the lanes; one FP64 conversion
+        // per group (or warp) leader
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            two_sum_acc(ah[q], al[q], __fadd_rn(pt[q].x, pt[q].y));
+            for (int o = span >> 1; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, ah[q], o);
+                const float ol = __shfl_xor_sync(0xffffffffu, al[q], o);
+                two_sum_acc(ah[q], al[q], oh);
+                al[q] = __fadd_rn(al[q], ol);
+            }
+        }
+        if ((tid & (span - 1)) == 0)
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                acc[q] = static_cast<double>(ah[q]) + static_cast<double>(al[q]);
+    } else {
+        for (int o = span >> 1; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    }
+    if (L <= 32) {
+        if (valid && lane == 0)
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                part[g][q] = acc[q];
+    } else {
+        if ((tid & 31) == 0)
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                wred[w][q] = acc[q];
+        __syncthreads();
+        const int wpg = L >> 5;
+        if (tid < K)
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                double sum = 0.0;
+                for (int u = 0; u < wpg; ++u)
+                    sum += wred[tid * wpg + u][q];
+                part[tid][q] = sum;
+            }
+    }
+    // the chunk area is also a TMA destination in later steps
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
 }
 
 // Start-up stores for slots [s0, s1) (all particles, in order).
@@ -364,6 +620,10 @@ __device__ void init_share(const EnsArgs &a, int off, int s0, int s1, int pass)
             for (int d = 0; d < 3; ++d) {
                 a.st[(F_A * 3 + d) * P + i] = a.anew[(0 + d) * P + i];
                 a.st[(F_J * 3 + d) * P + i] = a.anew[(3 + d) * P + i];
+                if (a.st32) {
+                    a.st32[(3 + d) * P + i] = __double2float_rn(a.anew[(0 + d) * P + i]);
+                    a.st32[(6 + d) * P + i] = __double2float_rn(a.anew[(3 + d) * P + i]);
+                }
             }
             continue;
         }
@@ -373,6 +633,10 @@ __device__ void init_share(const EnsArgs &a, int off, int s0, int s1, int pass)
             const double sv = a.anew[(6 + d) * P + i];
             a.st[(F_S * 3 + d) * P + i] = sv;
             a.st[(F_C * 3 + d) * P + i] = 0.0;
+            if (a.st32) {
+                a.st32[(9 + d) * P + i] = __double2float_rn(sv);
+                a.st32[(12 + d) * P + i] = 0.0f;
+            }
             na = fma(av, av, na);
             nj = fma(jv, jv, nj);
             ns = fma(sv, sv, ns);
@@ -398,9 +662,15 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
     __shared__ double red_d[32];
     __shared__ int red_i[32];
     __shared__ int s_job;
-    __shared__ double s_tmin;
-    __shared__ int s_cnt;
     __shared__ int s_fail;
+    __shared__ double s_min2[2];
+    __shared__ int s_cnt2[2];
+    __shared__ int s_cand[2][kSmall];
+    __shared__ int s_act[kSmall];
+    __shared__ int s_rcnt[8];
+    __shared__ double s_iv[kSmall][9];
+    __shared__ double s_part[kSmall][9];
+    __shared__ double s_wred[kEnsThreads / 32][9];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = static_cast<int>(cl.block_rank());
     const int G = static_cast<int>(cl.num_blocks());
@@ -448,56 +718,111 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
         }
 
         int64_t steps = 0;
+        const int T = blockDim.x;
+        const int per_t = (hi - lo + T - 1) / T;  // contiguous chunk per thread (ordered scans)
+        const int c0 = min(hi, lo + tid * per_t), c1 = min(hi, c0 + per_t);
         for (;;) {
-            // schedule: next time over the system
-            double mn = INFINITY;
-            for (int i = lo + tid; i < hi; i += blockDim.x)
-                mn = fmin(mn, a.t[i] + a.dt[i]);
-            mn = block_min(mn, red_d);
-            if (tid == 0)
-                s_tmin = mn;
+            const int par = static_cast<int>(steps & 1);
+            // schedule, one pass: the slice's earliest t_i + dt_i and how many
+            // particles reach it; a small set is listed in shared memory
+            double mt = INFINITY;
+            int ct = 0;
+            for (int i = c0; i < c1; ++i) {
+                const double tt = a.t[i] + a.dt[i];
+                if (tt < mt) {
+                    mt = tt;
+                    ct = 1;
+                } else if (tt == mt) {
+                    ++ct;
+                }
+            }
+            const double mb = block_min(mt, red_d);
+            const int mine = (mt == mb) ? ct : 0;
+            int tot_b = 0;
+            const int ex = block_exclusive_scan(mine, red_i, &tot_b);
+            if (mine > 0 && tot_b <= kSmall) {
+                int pos = ex;
+                for (int i = c0; i < c1; ++i)
+                    if (a.t[i] + a.dt[i] == mb)
+                        s_cand[par][pos++] = i;
+            }
+            if (tid == 0) {
+                s_min2[par] = mb;
+                s_cnt2[par] = tot_b;
+            }
             cl.sync();
             double tn = INFINITY;
             int fail = 0;
             for (int r = 0; r < G; ++r) {
-                tn = fmin(tn, *cl.map_shared_rank(&s_tmin, r));
+                tn = fmin(tn, *cl.map_shared_rank(&s_min2[par], r));
                 fail |= *cl.map_shared_rank(&s_fail, r);
             }
             if (tn > a.t_end || fail)
                 break;
-            int mine = 0, first = 0, tot = 0;
-            count_due(a, lo, hi, tn, mine, first);
-            const int ex = block_exclusive_scan(mine, red_i, &tot);
-            if (tid == 0)
-                s_cnt = tot;
-            cl.sync();
-            int prefix = 0, total = 0;
+            int total = 0, prefix = 0;
             for (int r = 0; r < G; ++r) {
-                const int v = *cl.map_shared_rank(&s_cnt, r);
+                const int v = (*cl.map_shared_rank(&s_min2[par], r) == tn) ? *cl.map_shared_rank(&s_cnt2[par], r) : 0;
                 prefix += r < rank ? v : 0;
                 total += v;
             }
-            {
-                int pos = prefix + ex;
-                const int per_t = (hi - lo + blockDim.x - 1) / blockDim.x;
-                for (int i = first; i < min(hi, first + per_t); ++i)
-                    if (a.t[i] + a.dt[i] == tn)
-                        a.act[off + pos++] = i;
+            if (total <= kSmall) {
+                // active list in ascending order from the blocks' lists, and
+                // its predicted values (the arithmetic of the j-records)
+                if (tid < G) {
+                    const int v = (*cl.map_shared_rank(&s_min2[par], tid) == tn) ? *cl.map_shared_rank(&s_cnt2[par], tid) : 0;
+                    s_rcnt[tid] = v;
+                }
+                __syncthreads();
+                for (int k = tid; k < total; k += T) {
+                    int base = 0, r = 0;
+                    while (k >= base + s_rcnt[r])
+                        base += s_rcnt[r++];
+                    const int i = *cl.map_shared_rank(&s_cand[par][k - base], r);
+                    s_act[k] = i;
+                    store_ivalues<MIXED>(a, i, tn, s_iv[k]);
+                }
+                __syncthreads();
+                eval_small<MIXED>(a, lo, hi, tn, total, s_iv, s_part, s_wred, smem, 2 * a.jtile);
+                cl.sync();
+                for (int k = tid; k < total; k += T) {
+                    const int i = s_act[k];
+                    if (i < lo || i >= hi)
+                        continue;
+                    double f[9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q)
+                        f[q] = 0.0;
+                    for (int r = 0; r < G; ++r) {
+                        const double *pr = cl.map_shared_rank(&s_part[k][0], r);
+#pragma unroll
+                        for (int q = 0; q < 9; ++q)
+                            f[q] += pr[q];
+                    }
+                    correct_one(a, i, tn, f);
+                }
+                __syncthreads();
+            } else {
+                if (mine > 0 && mb == tn) {
+                    int pos = prefix + ex;
+                    for (int i = c0; i < c1; ++i)
+                        if (a.t[i] + a.dt[i] == tn)
+                            a.act[off + pos++] = i;
+                }
+                predict_slice<MIXED>(a, lo, hi, tn);
+                cl.sync();
+                const int q = (total + G - 1) / G;
+                const int s0 = min(total, rank * q), s1 = min(total, s0 + q);
+                const bool ok = eval_share<MIXED>(a, off, nj, s0, s1, smem, bar, seq);
+                if (!ok && tid == 0)
+                    s_fail = 1;
+                __syncthreads();
+                if (ok)
+                    correct_share(a, off, s0, s1, tn);
+                cl.sync();
             }
-            predict_slice<MIXED>(a, lo, hi, tn);
-            cl.sync();
-            const int q = (total + G - 1) / G;
-            const int s0 = min(total, rank * q), s1 = min(total, s0 + q);
-            const bool ok = eval_share<MIXED>(a, off, nj, s0, s1, smem, bar, seq);
-            if (!ok && tid == 0)
-                s_fail = 1;
-            __syncthreads();
-            if (ok)
-                correct_share(a, off, s0, s1, tn);
             ++steps;
             if (rank == 0 && tid == 0)
                 atomicAdd(a.inter, static_cast<unsigned long long>(total) * static_cast<unsigned long long>(n));
-            cl.sync();
         }
         if (rank == 0 && tid == 0)
             a.steps[c] = steps;
@@ -584,6 +909,7 @@ EnsArgs make_args(nb_ensemble *e, int mode, double t_end)
     a.m = e->m;
     a.jb64 = e->jb64;
     a.jf32 = e->jf32;
+    a.st32 = e->st32;
     a.act = e->act;
     a.anew = e->anew;
     a.queue = e->queue;
@@ -648,6 +974,7 @@ void ens_free_all(nb_ensemble *e)
     cudaFree(e->anew);
     cudaFree(e->jb64);
     cudaFree(e->jf32);
+    cudaFree(e->st32);
     cudaFree(e->act);
     cudaFree(e->queue);
     cudaFree(e->steps);
@@ -775,6 +1102,8 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
     if (cf.precision == NB_MIXED) {
         EI(cudaMalloc(&e->jf32, 13 * P * sizeof(float)));
         EI(cudaMemsetAsync(e->jf32, 0, 13 * P * sizeof(float), e->stream));
+        EI(cudaMalloc(&e->st32, kSt32Rows * P * sizeof(float)));
+        EI(cudaMemsetAsync(e->st32, 0, kSt32Rows * P * sizeof(float), e->stream));
     } else {
         EI(cudaMalloc(&e->jb64, 5 * P * sizeof(double2)));
         EI(cudaMemsetAsync(e->jb64, 0, 5 * P * sizeof(double2), e->stream));
@@ -801,6 +1130,19 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
     EI(cudaMemcpyAsync(e->d_cnt, e->cnt.data(), n_systems * sizeof(int32_t), cudaMemcpyHostToDevice, e->stream));
     EI(cudaMemcpyAsync(e->d_order, order.data(), n_systems * sizeof(int32_t), cudaMemcpyHostToDevice, e->stream));
     EI(cudaMemcpyAsync(e->st, hst.data(), 18 * P * sizeof(double), cudaMemcpyHostToDevice, e->stream));
+    std::vector<float> h32;
+    if (e->st32) {  // FP32 copy of the starting x and v (a, jerk, snap, crackle start at 0)
+        h32.assign(kSt32Rows * P, 0.0f);
+        for (size_t q = 0; q < 3 * P; ++q) {
+            const double xv = hst[F_X * 3 * P + q], vv = hst[F_V * 3 * P + q];
+            const float xh = static_cast<float>(xv), vh = static_cast<float>(vv);
+            h32[15 * P + q] = xh;
+            h32[18 * P + q] = static_cast<float>(xv - static_cast<double>(xh));
+            h32[q] = vh;
+            h32[21 * P + q] = static_cast<float>(vv - static_cast<double>(vh));
+        }
+        EI(cudaMemcpyAsync(e->st32, h32.data(), kSt32Rows * P * sizeof(float), cudaMemcpyHostToDevice, e->stream));
+    }
     EI(cudaMemcpyAsync(e->m, hm.data(), P * sizeof(double), cudaMemcpyHostToDevice, e->stream));
     EI(cudaMemcpyAsync(e->t, ht.data(), P * sizeof(double), cudaMemcpyHostToDevice, e->stream));
     // padding particles: dt = +inf keeps them out of every schedule

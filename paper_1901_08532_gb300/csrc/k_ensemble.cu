@@ -385,13 +385,7 @@ __device__ void correct_one(const EnsArgs &a, int i, double tn, const double (&f
         *pj = j1;
         *ps = s1v;
         *pc = r.c1;
-        if (a.st32) {
-            store_xv32(a, i, d, r.x1, r.v1);
-            a.st32[(3 + d) * P + i] = __double2float_rn(a1);
-            a.st32[(6 + d) * P + i] = __double2float_rn(j1);
-            a.st32[(9 + d) * P + i] = __double2float_rn(s1v);
-            a.st32[(12 + d) * P + i] = __double2float_rn(r.c1);
-        }
+
         n2[0] = fma(a1, a1, n2[0]);
         n2[1] = fma(j1, j1, n2[1]);
         n2[2] = fma(s1v, s1v, n2[2]);
@@ -409,7 +403,98 @@ __device__ void correct_one(const EnsArgs &a, int i, double tn, const double (&f
         atomicOr(&a.ctl->err, NB_ERR_NONFINITE);
 }
 
+// |v| of a 3-vector in FP32 without overflow of the squares.
+__device__ __forceinline__ float norm3f(float x, float y, float z)
+{
+    const float m = fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z)));
+    if (m == 0.0f)
+        return 0.0f;
+    const float r = 1.0f / m;
+    const float u = x * r, v = y * r, w = z * r;
+    return m * sqrtf(fmaf(u, u, fmaf(v, v, w * w)));
+}
+
+// Mixed ensembles: the same corrector, interpolation and step with the
+// arithmetic in FP32 (the forces carry FP32 pair rounding already, about
+// 1e-7 of each sum's condition number): the velocity and position
+// increments are formed in FP32 and added to the FP64 state, the crackle,
+// pop and a^(5) of the quintic and the Aarseth criterion use FP32 copies of
+// the old derivatives.  h = tn - t_i is a power of two, so 1/h is exact.
+__device__ void correct_one_mixed(const EnsArgs &a, int i, double tn, const double (&f)[9])
+{
+    const size_t P = static_cast<size_t>(a.P);
+    const float h = __double2float_rn(tn - a.t[i]);
+    const float ih = 1.0f / h;
+    const float ih3 = ih * ih * ih;
+    float an[3], jn[3], sn[3], cn[3], dn[3], en[3];
+    bool finite = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float a0 = a.st32[(3 + d) * P + i], j0 = a.st32[(6 + d) * P + i], s0 = a.st32[(9 + d) * P + i];
+        const float a1 = __double2float_rn(f[d]), j1 = __double2float_rn(f[3 + d]);
+        const float s1 = __double2float_rn(f[6 + d]);
+        const float v0f = a.st32[d * P + i];
+        const float dv = h * fmaf(h, fmaf(h, (s0 + s1) * (1.0f / 120.0f), -(j1 - j0) * 0.1f), 0.5f * (a0 + a1));
+        const float v1f = v0f + dv;
+        const float dx = h * fmaf(h, fmaf(h, (j0 + j1) * (1.0f / 120.0f), -(a1 - a0) * 0.1f), 0.5f * (v0f + v1f));
+        double *px = a.st + (F_X * 3 + d) * P + i, *pv = a.st + (F_V * 3 + d) * P + i;
+        const double v1 = *pv + static_cast<double>(dv);
+        const double x1 = *px + static_cast<double>(dx);
+        const float R1 = a1 - fmaf(h, fmaf(0.5f * h, s0, j0), a0);
+        const float R2 = h * (j1 - fmaf(h, s0, j0));
+        const float R3 = h * h * (s1 - s0);
+        const float c1 = (60.0f * R1 - 36.0f * R2 + 9.0f * R3) * ih3;
+        const float d1 = (360.0f * R1 - 192.0f * R2 + 36.0f * R3) * ih3 * ih;
+        const float e1 = (720.0f * R1 - 360.0f * R2 + 60.0f * R3) * ih3 * ih * ih;
+        finite = finite && isfinite(x1) && isfinite(v1) && isfinite(c1);
+        *px = x1;
+        *pv = v1;
+        a.st[(F_A * 3 + d) * P + i] = f[d];
+        a.st[(F_J * 3 + d) * P + i] = f[3 + d];
+        a.st[(F_S * 3 + d) * P + i] = f[6 + d];
+        a.st[(F_C * 3 + d) * P + i] = static_cast<double>(c1);
+        store_xv32(a, i, d, x1, v1);
+        a.st32[(3 + d) * P + i] = a1;
+        a.st32[(6 + d) * P + i] = j1;
+        a.st32[(9 + d) * P + i] = s1;
+        a.st32[(12 + d) * P + i] = c1;
+        an[d] = a1;
+        jn[d] = j1;
+        sn[d] = s1;
+        cn[d] = c1;
+        dn[d] = d1;
+        en[d] = e1;
+    }
+    a.t[i] = tn;
+    bool hit = false;
+    if (a.dt_shared > 0.0) {
+        a.dt[i] = a.dt_shared;
+    } else {
+        // generalised Aarseth criterion eta (A1 / A4)^(1/3)
+        const float A1 = sqrtf(norm3f(an[0], an[1], an[2])) * sqrtf(norm3f(sn[0], sn[1], sn[2])) +
+                         norm3f(jn[0], jn[1], jn[2]);
+        const float A4 = sqrtf(norm3f(cn[0], cn[1], cn[2])) * sqrtf(norm3f(en[0], en[1], en[2])) +
+                         norm3f(dn[0], dn[1], dn[2]);
+        const float crit = static_cast<float>(a.eta) * cbrtf(A1 / A4);
+        a.dt[i] = quantise(static_cast<double>(crit), a.dt[i], tn, a.dt_min, a.dt_max, &hit);
+    }
+    if (hit)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->floor_hits), 1ull);
+    if (!finite)
+        atomicOr(&a.ctl->err, NB_ERR_NONFINITE);
+}
+
+template <bool MIXED>
+__device__ __forceinline__ void correct_particle(const EnsArgs &a, int i, double tn, const double (&f)[9])
+{
+    if (MIXED)
+        correct_one_mixed(a, i, tn, f);
+    else
+        correct_one(a, i, tn, f);
+}
+
 // Corrector for active slots [s0, s1) at time tn (new values in anew).
+template <bool MIXED>
 __device__ void correct_share(const EnsArgs &a, int off, int s0, int s1, double tn)
 {
     const size_t P = static_cast<size_t>(a.P);
@@ -418,7 +503,7 @@ __device__ void correct_share(const EnsArgs &a, int off, int s0, int s1, double 
 #pragma unroll
         for (int q = 0; q < 9; ++q)
             f[q] = a.anew[q * P + off + k];
-        correct_one(a, a.act[off + k], tn, f);
+        correct_particle<MIXED>(a, a.act[off + k], tn, f);
     }
 }
 
@@ -798,7 +883,7 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
                         for (int q = 0; q < 9; ++q)
                             f[q] += pr[q];
                     }
-                    correct_one(a, i, tn, f);
+                    correct_particle<MIXED>(a, i, tn, f);
                 }
                 __syncthreads();
             } else {
@@ -817,7 +902,7 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
                     s_fail = 1;
                 __syncthreads();
                 if (ok)
-                    correct_share(a, off, s0, s1, tn);
+                    correct_share<MIXED>(a, off, s0, s1, tn);
                 cl.sync();
             }
             ++steps;

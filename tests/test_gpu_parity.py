@@ -292,3 +292,25 @@ def test_full_size_sampled_parity(prec):
     kap = O.evaluate_kappa(m, x, v, a, eps, act[pick]) if prec else (None,) * 3
     for gq, rq, kq in zip(got, ref, kap):
         assert check_parity(prec, gq[pick], rq, kq) <= 1.0
+
+
+def test_bench_headline_launch_sampled_parity():
+    """The bench's headline step: N = 2^20 Plummer with Salpeter masses,
+    eps = 1e-4, every particle active, the mixed kernel in the automatic
+    launch shape (KI 2, 128 threads, j-tile 512, no split), on the start-up
+    state the bench uses; 32 evenly spread particles against the oracle."""
+    nb = nb_gpu()
+    n, eps = 1 << 20, 1e-4
+    m, x, v = ni.plummer(n, 3, imf="salpeter")
+    g = nb.NBody(m, x, v, eps, precision=nb.NB_MIXED, dt_shared=2.0 ** -10)
+    st = g.state()
+    shape = g.resolve_tiles(n)
+    assert (shape["ki"], shape["threads"], shape["jtile"], shape["split"]) == (2, 128, 512, 1)
+    g.predict(0.0)
+    got = g.evaluate(None)
+    g.close()
+    pick = np.linspace(0, n - 1, 32).astype(np.int32)
+    ref = O.evaluate(m, x, v, st["a"], eps, pick)
+    kap = O.evaluate_kappa(m, x, v, st["a"], eps, pick)
+    for gq, rq, kq in zip(got, ref, kap):
+        assert check_parity(1, gq[pick], rq, kq) <= 1.0

@@ -602,11 +602,12 @@ def ensemble_bench(args):
     out = {"workload": f"ensemble_{args.ens_systems}_plummer_N256-16384_eps1e-4",
            "systems": int(sizes.size), "particles": int(sizes.sum())}
     precs = ("mixed", "fp64") if args.prec == "both" else (args.prec,)
+    prec_of = {"mixed": nb.NB_MIXED, "fp64": nb.NB_FP64, "ex": nb.NB_EX}
     shapes = [tuple(int(q) for q in sh.split("x")) for sh in args.ens_shapes.split(",")]
     shapes = [sh if len(sh) == 3 else (sh[0], sh[1], 0) for sh in shapes]
     everyone = list(range(sizes.size))
     for prec_name in precs:
-        prec = nb.NB_MIXED if prec_name == "mixed" else nb.NB_FP64
+        prec = prec_of[prec_name]
         res = {"t_end": args.ens_t_end, "shapes": {}}
         for sh in shapes:
             r = run_ens(everyone, prec, sh, args.ens_t_end)

@@ -74,8 +74,7 @@ typedef enum {
                      double word hi + lo of FP32 numbers (about 48 mantissa
                      bits, FP32 exponent range) and the whole pair term
                      computed in double-word arithmetic from FP32
-                     operations; per-tile sums added in FP64; not available
-                     for ensembles                                           */
+                     operations; per-tile sums added in FP64              */
 } nb_precision;
 
 /* Shape of the evaluation launch.  0 in any field means "choose
@@ -254,7 +253,11 @@ typedef struct nb_ensemble nb_ensemble;
  * fields as nb_init (tiles and start_forces are ignored; the starting forces
  * and steps are always computed, in one launch).  The ensemble runs on
  * cfg->stream, or on a stream of its own when that is NULL (graph capture
- * needs a stream other than the legacy default stream).
+ * needs a stream other than the legacy default stream).  Precision NB_FP64,
+ * NB_MIXED or NB_EX (NB_SP is rejected).  NB_MIXED ensembles also run the
+ * predictor (from an FP32 copy of the state, x and v as double words) and
+ * the corrector's increments and step criterion in FP32; NB_FP64 and NB_EX
+ * use the FP64 predictor and corrector.
  * Errors: NB_EINVAL, NB_ENONFINITE, NB_ENOMEM, NB_ECUDA. */
 nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *sizes,
                            const double *m, const double *x, const double *v, double eps,
@@ -262,7 +265,8 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
 
 /* Launch shape: thread blocks per system (1..8, one hardware cluster),
  * threads per block (64..256, multiple of 32), j-tile length (multiple of 4).
- * Defaults: 4 blocks of 128 threads, j-tile 1024 (NB_MIXED) or 512 (NB_FP64). */
+ * Defaults: 4 blocks of 128 threads, j-tile 1024 (NB_MIXED) or 512 (NB_FP64,
+ * NB_EX). */
 nb_status nb_ensemble_set_shape(nb_ensemble *e, int32_t ctas_per_system, int32_t threads,
                                 int32_t jtile);
 

@@ -155,7 +155,7 @@ class NBody:
     """One N-body system on the current CUDA device (a libnb context).
 
     m[n], x[n,3], v[n,3] are host arrays (copied); eps > 0.  precision is
-    NB_FP64, NB_MIXED, NB_SP or NB_EX (the last two NBody only).  stream: a torch.cuda.Stream or raw cudaStream_t
+    NB_FP64, NB_MIXED, NB_SP or NB_EX (NB_SP NBody only).  stream: a torch.cuda.Stream or raw cudaStream_t
     (default: torch's current stream).
     """
 

@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "nb_device.cuh"
+#include "nb_ff.cuh"
 #include "nb_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -194,9 +195,10 @@ __device__ __forceinline__ void store_xv32(const EnsArgs &a, int i, int k, doubl
     a.st32[(21 + k) * P + i] = __double2float_rn(v - static_cast<double>(vh));
 }
 
-template <bool MIXED>
+template <int PR>
 __device__ void predict_slice(const EnsArgs &a, int lo, int hi, double tp)
 {
+    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
     const size_t P = static_cast<size_t>(a.P);
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         if (MIXED) {
@@ -210,6 +212,23 @@ __device__ void predict_slice(const EnsArgs &a, int lo, int hi, double tp)
                 a.jf32[(10 + k) * P + i] = r.a[k];
             }
             a.jf32[3 * P + i] = __double2float_rn(a.m[i]);
+        } else if (EXP) {
+            // 20 FP32 rows: hi then lo of x, v, a (three rows each), m hi, m lo
+            Taylor p[3];
+            predict_one(a, i, tp, p);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double q[3] = {p[k].x, p[k].v, p[k].a};
+#pragma unroll
+                for (int g = 0; g < 3; ++g) {
+                    const float h = __double2float_rn(q[g]);
+                    a.jf32[(6 * g + k) * P + i] = h;
+                    a.jf32[(6 * g + 3 + k) * P + i] = __double2float_rn(q[g] - static_cast<double>(h));
+                }
+            }
+            const float mh = __double2float_rn(a.m[i]);
+            a.jf32[18 * P + i] = mh;
+            a.jf32[19 * P + i] = __double2float_rn(a.m[i] - static_cast<double>(mh));
         } else {
             Taylor p[3];
             predict_one(a, i, tp, p);
@@ -224,17 +243,19 @@ __device__ void predict_slice(const EnsArgs &a, int lo, int hi, double tp)
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-template <bool MIXED>
+template <int PR>
 __device__ __forceinline__ void issue_ens_tile(const EnsArgs &a, unsigned char *smem, uint64_t *bar,
                                                int stage, int j0, int len)
 {
+    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
     const int jt = a.jtile;
     const size_t P = static_cast<size_t>(a.P);
-    if (MIXED) {
-        float *dst = reinterpret_cast<float *>(smem) + static_cast<size_t>(stage) * NCF * jt;
-        mbar_expect_tx(&bar[stage], static_cast<uint32_t>(NCF * len * 4));
+    if (MIXED || EXP) {
+        constexpr int NR = EXP ? NCX : NCF;
+        float *dst = reinterpret_cast<float *>(smem) + static_cast<size_t>(stage) * NR * jt;
+        mbar_expect_tx(&bar[stage], static_cast<uint32_t>(NR * len * 4));
 #pragma unroll
-        for (int r = 0; r < NCF; ++r)
+        for (int r = 0; r < NR; ++r)
             bulk_g2s(dst + r * jt, a.jf32 + r * P + j0, static_cast<uint32_t>(len * 4), &bar[stage]);
     } else {
         double2 *dst = reinterpret_cast<double2 *>(smem) + static_cast<size_t>(stage) * 5 * jt;
@@ -247,10 +268,11 @@ __device__ __forceinline__ void issue_ens_tile(const EnsArgs &a, unsigned char *
 
 // Evaluate active slots [s0, s1) of the system starting at `off` against its
 // nj j-records.  Returns false if a TMA wait timed out (uniform in the CTA).
-template <bool MIXED>
+template <int PR>
 __device__ bool eval_share(const EnsArgs &a, int off, int nj, int s0, int s1, unsigned char *smem,
                            uint64_t *bar, unsigned &seq)
 {
+    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
     const int T = blockDim.x, tid = threadIdx.x, jt = a.jtile;
     const int m = s1 - s0;
     if (m <= 0)
@@ -277,8 +299,16 @@ __device__ bool eval_share(const EnsArgs &a, int off, int nj, int s0, int s1, un
         // i-particle data (the same predicted records the j-loop reads)
         float2 ni[12];
         float hi[9], lo[9];
+        ExI<float2> nie;
         double xi = 0, yi = 0, zi = 0, vxi = 0, vyi = 0, vzi = 0, axi = 0, ayi = 0, azi = 0;
-        if (MIXED) {
+        if (EXP) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                nie.x[k] = {f2(-a.jf32[k * P + i]), f2(-a.jf32[(3 + k) * P + i])};
+                nie.v[k] = {f2(-a.jf32[(6 + k) * P + i]), f2(-a.jf32[(9 + k) * P + i])};
+                nie.a[k] = {f2(-a.jf32[(12 + k) * P + i]), f2(-a.jf32[(15 + k) * P + i])};
+            }
+        } else if (MIXED) {
 #pragma unroll
             for (int q = 0; q < 12; ++q)
                 ni[q] = f2(-a.jf32[kRow[q] * P + i]);
@@ -294,7 +324,7 @@ __device__ bool eval_share(const EnsArgs &a, int off, int nj, int s0, int s1, un
         }
         if (tid == 0)
             for (int q = 0; q < min(2, ntiles); ++q)
-                issue_ens_tile<MIXED>(a, smem, bar, (seq + q) & 1, off + q * jt, min(jt, nj - q * jt));
+                issue_ens_tile<PR>(a, smem, bar, (seq + q) & 1, off + q * jt, min(jt, nj - q * jt));
         for (int tl = 0; tl < ntiles; ++tl) {
             const unsigned sq = seq + tl;
             const int stg = sq & 1;
@@ -308,7 +338,26 @@ __device__ bool eval_share(const EnsArgs &a, int off, int nj, int s0, int s1, un
                 return false;
             }
             const int len = min(jt, nj - tl * jt);
-            if (MIXED) {
+            if (EXP) {
+                const float *s = reinterpret_cast<const float *>(smem) + static_cast<size_t>(stg) * NCX * jt;
+                const float e2h = __double2float_rn(a.eps2);
+                const ff::FF<float2> eps2x = {f2(e2h), f2(__double2float_rn(a.eps2 - static_cast<double>(e2h)))};
+                ff::FF<float2> part[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    part[q] = {f2(0.0f), f2(0.0f)};
+                for (int jj = 2 * lj; jj < len; jj += 2 * lanes) {
+                    float2 c[NCX];
+#pragma unroll
+                    for (int r = 0; r < NCX; ++r)
+                        c[r] = *reinterpret_cast<const float2 *>(s + r * jt + jj);
+                    pair_ex(c, nie, eps2x, part);
+                }
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    acc[q] += (static_cast<double>(part[q].h.x) + static_cast<double>(part[q].l.x)) +
+                              (static_cast<double>(part[q].h.y) + static_cast<double>(part[q].l.y));
+            } else if (MIXED) {
                 const float *s = reinterpret_cast<const float *>(smem) + static_cast<size_t>(stg) * NCF * jt;
                 float2 part[9];
 #pragma unroll
@@ -343,7 +392,7 @@ __device__ bool eval_share(const EnsArgs &a, int off, int nj, int s0, int s1, un
             }
             __syncthreads();
             if (tid == 0 && tl + 2 < ntiles)
-                issue_ens_tile<MIXED>(a, smem, bar, stg, off + (tl + 2) * jt, min(jt, nj - (tl + 2) * jt));
+                issue_ens_tile<PR>(a, smem, bar, stg, off + (tl + 2) * jt, min(jt, nj - (tl + 2) * jt));
         }
         seq += ntiles;
         if (MIXED)
@@ -484,9 +533,10 @@ __device__ void correct_one_mixed(const EnsArgs &a, int i, double tn, const doub
         atomicOr(&a.ctl->err, NB_ERR_NONFINITE);
 }
 
-template <bool MIXED>
+template <int PR>
 __device__ __forceinline__ void correct_particle(const EnsArgs &a, int i, double tn, const double (&f)[9])
 {
+    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
     if (MIXED)
         correct_one_mixed(a, i, tn, f);
     else
@@ -494,16 +544,17 @@ __device__ __forceinline__ void correct_particle(const EnsArgs &a, int i, double
 }
 
 // Corrector for active slots [s0, s1) at time tn (new values in anew).
-template <bool MIXED>
+template <int PR>
 __device__ void correct_share(const EnsArgs &a, int off, int s0, int s1, double tn)
 {
+    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
     const size_t P = static_cast<size_t>(a.P);
     for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
         double f[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q)
             f[q] = a.anew[q * P + off + k];
-        correct_particle<MIXED>(a, a.act[off + k], tn, f);
+        correct_particle<PR>(a, a.act[off + k], tn, f);
     }
 }
 
@@ -517,9 +568,10 @@ constexpr int kSmall = 16;
 // i-values of the small active set: FP64 x, v, a; in mixed precision the
 // same slots hold 12 negated FP32 values (x_hi, x_lo, v, a) of the record the
 // predictor writes for particle i.
-template <bool MIXED>
+template <int PR>
 __device__ __forceinline__ void store_ivalues(const EnsArgs &a, int i, double tn, double *iv)
 {
+    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
     if (MIXED) {
         MixedRec r;
         predict_one_mixed(a, i, tn, r);
@@ -530,6 +582,21 @@ __device__ __forceinline__ void store_ivalues(const EnsArgs &a, int i, double tn
             f[3 + k] = -r.xl[k];
             f[6 + k] = -r.v[k];
             f[9 + k] = -r.a[k];
+        }
+    } else if (EXP) {
+        // 18 negated FP32 values: hi then lo of x, v, a (the j-record's split)
+        Taylor p[3];
+        predict_one(a, i, tn, p);
+        float *f = reinterpret_cast<float *>(iv);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double q[3] = {p[k].x, p[k].v, p[k].a};
+#pragma unroll
+            for (int g = 0; g < 3; ++g) {
+                const float h = __double2float_rn(q[g]);
+                f[6 * g + k] = -h;
+                f[6 * g + 3 + k] = -__double2float_rn(q[g] - static_cast<double>(h));
+            }
         }
     } else {
         Taylor p[3];
@@ -546,14 +613,15 @@ __device__ __forceinline__ void store_ivalues(const EnsArgs &a, int i, double tn
 // Partial sums of the K active particles (i-values in iv) over the j of
 // [lo, hi), written to part[K][9].  The j are predicted to tn chunk by chunk
 // straight into shared memory (cap records per chunk, the layout of the
-// evaluation buffer: 13 FP32 rows, or 5 rows of double2), so the sums read
+// evaluation buffer: 13 or 20 FP32 rows, or 5 rows of double2), so the sums read
 // on-chip data only.  L = T / K2 lanes per active particle (K2 the power of
 // two >= K); lanes take every L-th j (pair of j in mixed precision) and are
 // combined in a fixed order.
-template <bool MIXED>
+template <int PR>
 __device__ void eval_small(const EnsArgs &a, int lo, int hi, double tn, int K, const double (*iv)[9],
                            double (*part)[9], double (*wred)[9], unsigned char *smem, int cap)
 {
+    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
     const int T = blockDim.x, tid = threadIdx.x;
     int K2 = 1;
     while (K2 < K)
@@ -573,6 +641,20 @@ __device__ void eval_small(const EnsArgs &a, int lo, int hi, double tn, int K, c
     for (int q = 0; q < 9; ++q)
         ah[q] = al[q] = 0.0f;
     int cnt = 0;
+    ExI<float2> nie;
+    ff::FF<float2> px[9];
+    if (EXP) {
+        const float *ivf = reinterpret_cast<const float *>(iv[gi]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            nie.x[k] = {f2(ivf[k]), f2(ivf[3 + k])};
+            nie.v[k] = {f2(ivf[6 + k]), f2(ivf[9 + k])};
+            nie.a[k] = {f2(ivf[12 + k]), f2(ivf[15 + k])};
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            px[q] = {f2(0.0f), f2(0.0f)};
+    }
     if (MIXED) {
         const float *ivf = reinterpret_cast<const float *>(iv[gi]);
 #pragma unroll
@@ -600,6 +682,22 @@ __device__ void eval_small(const EnsArgs &a, int lo, int hi, double tn, int K, c
                     sf[(10 + k) * cap + u] = r.a[k];
                 }
                 sf[3 * cap + u] = __double2float_rn(mj);
+            } else if (EXP) {
+                Taylor p[3];
+                predict_one(a, b + u, tn, p);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const double q[3] = {p[k].x, p[k].v, p[k].a};
+#pragma unroll
+                    for (int gg = 0; gg < 3; ++gg) {
+                        const float h = __double2float_rn(q[gg]);
+                        sf[(6 * gg + k) * cap + u] = h;
+                        sf[(6 * gg + 3 + k) * cap + u] = __double2float_rn(q[gg] - static_cast<double>(h));
+                    }
+                }
+                const float mh = __double2float_rn(mj);
+                sf[18 * cap + u] = mh;
+                sf[19 * cap + u] = __double2float_rn(mj - static_cast<double>(mh));
             } else {
                 Taylor p[3];
                 predict_one(a, b + u, tn, p);
@@ -611,7 +709,35 @@ __device__ void eval_small(const EnsArgs &a, int lo, int hi, double tn, int K, c
             }
         }
         __syncthreads();
-        if (MIXED) {
+        if (EXP) {
+            const float e2h = __double2float_rn(a.eps2);
+            const ff::FF<float2> eps2x = {f2(e2h), f2(__double2float_rn(a.eps2 - static_cast<double>(e2h)))};
+            for (int jj = 2 * lane; jj < len; jj += 2 * L) {
+                float2 c[NCX];
+                if (jj + 1 < len) {
+#pragma unroll
+                    for (int r = 0; r < NCX; ++r)
+                        c[r] = *reinterpret_cast<const float2 *>(sf + r * cap + jj);
+                } else {
+                    // odd tail: the second half repeats the first j with no mass
+#pragma unroll
+                    for (int r = 0; r < NCX; ++r) {
+                        const float x0 = sf[r * cap + jj];
+                        c[r] = make_float2(x0, r >= 18 ? 0.0f : x0);
+                    }
+                }
+                pair_ex(c, nie, eps2x, px);
+                if (++cnt == 32) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        acc[q] += (static_cast<double>(px[q].h.x) + static_cast<double>(px[q].l.x)) +
+                                  (static_cast<double>(px[q].h.y) + static_cast<double>(px[q].l.y));
+                        px[q] = {f2(0.0f), f2(0.0f)};
+                    }
+                    cnt = 0;
+                }
+            }
+        } else if (MIXED) {
             for (int jj = 2 * lane; jj < len; jj += 2 * L) {
                 float2 c[NCF];
                 if (jj + 1 < len) {
@@ -646,6 +772,11 @@ __device__ void eval_small(const EnsArgs &a, int lo, int hi, double tn, int K, c
     }
     const int w = tid >> 5;
     const int span = L < 32 ? L : 32;  // lanes combined by shuffles
+    if (EXP)
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            acc[q] += (static_cast<double>(px[q].h.x) + static_cast<double>(px[q].l.x)) +
+                      (static_cast<double>(px[q].h.y) + static_cast<double>(px[q].l.y));
     if (MIXED) {
         // fixed-order double-word sums across the lanes; one FP64 conversion
         // per group (or warp) leader
@@ -739,9 +870,10 @@ __device__ void init_share(const EnsArgs &a, int off, int s0, int s1, int pass)
     }
 }
 
-template <bool MIXED>
+template <int PR>
 __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
 {
+    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ double red_d[32];
@@ -782,7 +914,7 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
             break;
         const int c = a.order[job];
         const int off = a.off[c], n = a.cnt[c];
-        const int nj = MIXED ? (n + 3) / 4 * 4 : n;
+        const int nj = (MIXED || EXP) ? (n + 3) / 4 * 4 : n;
         const int per = (n + G - 1) / G;
         const int lo = off + min(n, rank * per), hi = off + min(n, (rank + 1) * per);
 
@@ -790,9 +922,9 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
             for (int k = lo - off + tid; k < hi - off; k += blockDim.x)
                 a.act[off + k] = off + k;
             for (int pass = 0; pass < 2; ++pass) {
-                predict_slice<MIXED>(a, lo, hi, 0.0);
+                predict_slice<PR>(a, lo, hi, 0.0);
                 cl.sync();
-                const bool ok = eval_share<MIXED>(a, off, nj, lo - off, hi - off, smem, bar, seq);
+                const bool ok = eval_share<PR>(a, off, nj, lo - off, hi - off, smem, bar, seq);
                 if (!ok && tid == 0)
                     s_fail = 1;
                 __syncthreads();
@@ -864,10 +996,10 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
                         base += s_rcnt[r++];
                     const int i = *cl.map_shared_rank(&s_cand[par][k - base], r);
                     s_act[k] = i;
-                    store_ivalues<MIXED>(a, i, tn, s_iv[k]);
+                    store_ivalues<PR>(a, i, tn, s_iv[k]);
                 }
                 __syncthreads();
-                eval_small<MIXED>(a, lo, hi, tn, total, s_iv, s_part, s_wred, smem, 2 * a.jtile);
+                eval_small<PR>(a, lo, hi, tn, total, s_iv, s_part, s_wred, smem, 2 * a.jtile);
                 cl.sync();
                 for (int k = tid; k < total; k += T) {
                     const int i = s_act[k];
@@ -883,7 +1015,7 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
                         for (int q = 0; q < 9; ++q)
                             f[q] += pr[q];
                     }
-                    correct_particle<MIXED>(a, i, tn, f);
+                    correct_particle<PR>(a, i, tn, f);
                 }
                 __syncthreads();
             } else {
@@ -893,16 +1025,16 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
                         if (a.t[i] + a.dt[i] == tn)
                             a.act[off + pos++] = i;
                 }
-                predict_slice<MIXED>(a, lo, hi, tn);
+                predict_slice<PR>(a, lo, hi, tn);
                 cl.sync();
                 const int q = (total + G - 1) / G;
                 const int s0 = min(total, rank * q), s1 = min(total, s0 + q);
-                const bool ok = eval_share<MIXED>(a, off, nj, s0, s1, smem, bar, seq);
+                const bool ok = eval_share<PR>(a, off, nj, s0, s1, smem, bar, seq);
                 if (!ok && tid == 0)
                     s_fail = 1;
                 __syncthreads();
                 if (ok)
-                    correct_share<MIXED>(a, off, s0, s1, tn);
+                    correct_share<PR>(a, off, s0, s1, tn);
                 cl.sync();
             }
             ++steps;
@@ -935,15 +1067,22 @@ nb_status ecuda(nb_ensemble *e, cudaError_t c, const char *where)
             return ecuda((e), e_, #call);           \
     } while (0)
 
-size_t ens_smem(const nb_ensemble *e)
+// Kernel instantiation of a precision: 0 FP64, 1 mixed, 2 EX.
+int ens_kind(const nb_ensemble *e)
 {
-    const bool mixed = e->cfg.precision == NB_MIXED;
-    return static_cast<size_t>(2) * (mixed ? NCF * 4 : 5 * 16) * e->jtile;
+    return e->cfg.precision == NB_MIXED ? 1 : (e->cfg.precision == NB_EX ? 2 : 0);
 }
 
-template <bool MIXED>
+size_t ens_smem(const nb_ensemble *e)
+{
+    const int k = ens_kind(e);
+    return static_cast<size_t>(2) * (k == 1 ? NCF * 4 : (k == 2 ? NCX * 4 : 5 * 16)) * e->jtile;
+}
+
+template <int PR>
 cudaError_t launch_ens(nb_ensemble *e, const EnsArgs &a, int grid_clusters)
 {
+    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid_clusters * e->G);
     cfg.blockDim = dim3(e->threads);
@@ -956,13 +1095,14 @@ cudaError_t launch_ens(nb_ensemble *e, const EnsArgs &a, int grid_clusters)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, ensemble_kernel<MIXED>, a);
+    return cudaLaunchKernelEx(&cfg, ensemble_kernel<PR>, a);
 }
 
-template <bool MIXED>
+template <int PR>
 cudaError_t max_clusters(nb_ensemble *e, int *out)
 {
-    cudaError_t err = cudaFuncSetAttribute(ensemble_kernel<MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
+    cudaError_t err = cudaFuncSetAttribute(ensemble_kernel<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(ens_smem(e)));
     if (err != cudaSuccess)
         return err;
@@ -977,7 +1117,7 @@ cudaError_t max_clusters(nb_ensemble *e, int *out)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(out, ensemble_kernel<MIXED>, &cfg);
+    return cudaOccupancyMaxActiveClusters(out, ensemble_kernel<PR>, &cfg);
 }
 
 EnsArgs make_args(nb_ensemble *e, int mode, double t_end)
@@ -1016,15 +1156,15 @@ EnsArgs make_args(nb_ensemble *e, int mode, double t_end)
 // Enqueue one persistent launch (queue reset + kernel) on e->stream.
 nb_status enqueue_run(nb_ensemble *e, int mode, double t_end)
 {
-    const bool mixed = e->cfg.precision == NB_MIXED;
     int maxc = 0;
-    ECU(e, mixed ? max_clusters<true>(e, &maxc) : max_clusters<false>(e, &maxc));
+    const int kind = ens_kind(e);
+    ECU(e, kind == 1 ? max_clusters<1>(e, &maxc) : (kind == 2 ? max_clusters<2>(e, &maxc) : max_clusters<0>(e, &maxc)));
     if (maxc < 1)
         return efail(e, NB_EINVAL, "ensemble launch shape does not fit on an SM");
     const int grid = std::min(maxc, e->nc);
     ECU(e, cudaMemsetAsync(e->queue, 0, sizeof(int), e->stream));
     const EnsArgs a = make_args(e, mode, t_end);
-    ECU(e, mixed ? launch_ens<true>(e, a, grid) : launch_ens<false>(e, a, grid));
+    ECU(e, kind == 1 ? launch_ens<1>(e, a, grid) : (kind == 2 ? launch_ens<2>(e, a, grid) : launch_ens<0>(e, a, grid)));
     return NB_OK;
 }
 
@@ -1098,13 +1238,14 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
         nb_set_thread_error("n_systems >= 1 and non-NULL sizes, m, x, v are required");
         return NB_EINVAL;
     }
-    if ((cf.precision != NB_FP64 && cf.precision != NB_MIXED) || !(cf.eta > 0) || !(cf.eta_s > 0) ||
+    if ((cf.precision != NB_FP64 && cf.precision != NB_MIXED && cf.precision != NB_EX) || !(cf.eta > 0) ||
+        !(cf.eta_s > 0) ||
         !pow2(cf.dt_min) || !pow2(cf.dt_max) || cf.dt_min > cf.dt_max ||
         (cf.dt_shared != 0.0 && !pow2(cf.dt_shared))) {
         nb_set_thread_error("invalid configuration");
         return NB_EINVAL;
     }
-    const double eps_min = cf.precision == NB_MIXED ? std::ldexp(1.0, -40) : std::ldexp(1.0, -60);
+    const double eps_min = cf.precision != NB_FP64 ? std::ldexp(1.0, -40) : std::ldexp(1.0, -60);
     if (!(eps >= eps_min) || !(eps <= 1e18)) {
         nb_set_thread_error("eps out of range");
         return NB_EINVAL;
@@ -1138,7 +1279,7 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
     e->eps = eps;
     e->nc = n_systems;
     e->P = padded;
-    e->jtile = cf.precision == NB_MIXED ? 1024 : 512;
+    e->jtile = cf.precision == NB_MIXED ? 1024 : 512;  // FP64 and EX: 512
     auto bail = [&](nb_status s) {
         nb_set_thread_error(e->err.c_str());
         ens_free_all(e);
@@ -1189,6 +1330,9 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
         EI(cudaMemsetAsync(e->jf32, 0, 13 * P * sizeof(float), e->stream));
         EI(cudaMalloc(&e->st32, kSt32Rows * P * sizeof(float)));
         EI(cudaMemsetAsync(e->st32, 0, kSt32Rows * P * sizeof(float), e->stream));
+    } else if (cf.precision == NB_EX) {
+        EI(cudaMalloc(&e->jf32, NCX * P * sizeof(float)));
+        EI(cudaMemsetAsync(e->jf32, 0, NCX * P * sizeof(float), e->stream));
     } else {
         EI(cudaMalloc(&e->jb64, 5 * P * sizeof(double2)));
         EI(cudaMemsetAsync(e->jb64, 0, 5 * P * sizeof(double2), e->stream));
@@ -1300,7 +1444,8 @@ nb_status nb_ensemble_run(nb_ensemble *e, double t_end, int use_graph)
         }
         // occupancy query and attributes before capture
         int maxc = 0;
-        ECU(e, e->cfg.precision == NB_MIXED ? max_clusters<true>(e, &maxc) : max_clusters<false>(e, &maxc));
+        const int kind = ens_kind(e);
+        ECU(e, kind == 1 ? max_clusters<1>(e, &maxc) : (kind == 2 ? max_clusters<2>(e, &maxc) : max_clusters<0>(e, &maxc)));
         ECU(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
         nb_status s = enqueue_run(e, 0, t_end);
         cudaGraph_t g = nullptr;

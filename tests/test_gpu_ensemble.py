@@ -26,11 +26,14 @@ def _concat(ms, xs, vs):
     return np.concatenate(ms), np.concatenate(xs), np.concatenate(vs)
 
 
-def test_fp64_ensemble_matches_oracle_per_system():
+@pytest.mark.parametrize("prec", [0, 3])
+def test_fp64_and_ex_ensembles_match_oracle_per_system(prec):
+    """FP64 and EX (double-word) ensembles take the oracle's step decisions
+    system by system and end on its state to 1e-10."""
     nb = nb_gpu()
     ms, xs, vs = _systems(SIZES)
     eps, t_end = 1e-4, 0.125
-    ens = nb.Ensemble(SIZES, *_concat(ms, xs, vs), eps)
+    ens = nb.Ensemble(SIZES, *_concat(ms, xs, vs), eps, precision=prec)
     ens.run(t_end)
     st = ens.state()
     steps, inter, _ = ens.stats()
@@ -104,3 +107,24 @@ def test_graph_replay_continues_the_integration():
     for f in ("x", "v", "a", "j", "s", "t", "dt"):
         np.testing.assert_array_equal(sa[f], sb[f])
     assert launches == 3  # start-up + two graph launches
+
+
+def test_ex_ensemble_launch_shapes_agree_and_track_fp64():
+    nb = nb_gpu()
+    ms, xs, vs = _systems(SIZES, 70)
+    out = []
+    for g, thr in ((1, 128), (4, 128), (8, 64)):
+        ens = nb.Ensemble(SIZES, *_concat(ms, xs, vs), 1e-4, precision=nb.NB_EX, dt_max=2.0 ** -5)
+        ens.set_shape(g, thr)
+        ens.run(2.0 ** -5)
+        out.append(ens.state())
+        ens.close()
+    ref = nb.Ensemble(SIZES, *_concat(ms, xs, vs), 1e-4, dt_max=2.0 ** -5)
+    ref.run(2.0 ** -5)
+    st64 = ref.state()
+    ref.close()
+    for st in out:
+        for f in ("x", "v"):
+            assert rel_err(st[f], out[0][f]).max() < 1e-12, f
+            assert rel_err(st[f], st64[f]).max() < 1e-11, f
+        np.testing.assert_array_equal(st["t"], st64["t"])

@@ -83,8 +83,9 @@ def parse():
                         "(seed 4), each to --ens-t-end; one persistent launch vs one at a time")
     p.add_argument("--ens-t-end", type=float, default=0.25)
     p.add_argument("--ens-systems", type=int, default=256)
-    p.add_argument("--ens-shapes", default="4x128",
-                   help="comma-separated ctas_per_system x threads [x jtile] shapes to time")
+    p.add_argument("--ens-shapes", default="",
+                   help="comma-separated ctas_per_system x threads [x jtile] shapes to time "
+                        "(default: 4x128 for mixed, 8x128 for fp64 and ex)")
     p.add_argument("--ens-sample", type=int, default=8,
                    help="systems in the one-at-a-time comparison (0: skip)")
     p.add_argument("--ens-cmp-t-end", type=float, default=0.125)
@@ -603,12 +604,15 @@ def ensemble_bench(args):
            "systems": int(sizes.size), "particles": int(sizes.sum())}
     precs = ("mixed", "fp64") if args.prec == "both" else (args.prec,)
     prec_of = {"mixed": nb.NB_MIXED, "fp64": nb.NB_FP64, "ex": nb.NB_EX}
-    shapes = [tuple(int(q) for q in sh.split("x")) for sh in args.ens_shapes.split(",")]
-    shapes = [sh if len(sh) == 3 else (sh[0], sh[1], 0) for sh in shapes]
+    def shapes_for(prec_name):
+        spec = args.ens_shapes or ("4x128" if prec_name == "mixed" else "8x128")
+        out = [tuple(int(q) for q in sh.split("x")) for sh in spec.split(",")]
+        return [sh if len(sh) == 3 else (sh[0], sh[1], 0) for sh in out]
     everyone = list(range(sizes.size))
     for prec_name in precs:
         prec = prec_of[prec_name]
         res = {"t_end": args.ens_t_end, "shapes": {}}
+        shapes = shapes_for(prec_name)
         for sh in shapes:
             r = run_ens(everyone, prec, sh, args.ens_t_end)
             res["shapes"]["%dx%dx%d" % sh] = r

@@ -265,8 +265,8 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
 
 /* Launch shape: thread blocks per system (1..8, one hardware cluster),
  * threads per block (64..256, multiple of 32), j-tile length (multiple of 4).
- * Defaults: 4 blocks of 128 threads, j-tile 1024 (NB_MIXED) or 512 (NB_FP64,
- * NB_EX). */
+ * Defaults: NB_MIXED 4 blocks of 128 threads, j-tile 1024; NB_FP64 and NB_EX
+ * 8 blocks of 128 threads, j-tile 512. */
 nb_status nb_ensemble_set_shape(nb_ensemble *e, int32_t ctas_per_system, int32_t threads,
                                 int32_t jtile);
 

@@ -370,7 +370,11 @@ class Ensemble:
         if st != NB_OK:
             raise NBError(st, _lib.nb_ensemble_last_error(self._e).decode())
 
-    def set_shape(self, ctas_per_system=4, threads=128, jtile=None):
+    def set_shape(self, ctas_per_system=None, threads=128, jtile=None):
+        """Blocks per system, threads per block, j-tile length (None: the
+        library's default for the precision)."""
+        if ctas_per_system is None:
+            ctas_per_system = 4 if self.precision == NB_MIXED else 8
         if jtile is None:
             jtile = 1024 if self.precision == NB_MIXED else 512
         self._check(_lib.nb_ensemble_set_shape(self._e, int(ctas_per_system), int(threads), int(jtile)))

@@ -56,7 +56,7 @@ struct nb_ensemble {
     int64_t *steps = nullptr;
     unsigned long long *inter = nullptr;
     nb_ctl *ctl = nullptr, *ctl_h = nullptr;
-    int G = 4, threads = 128, jtile = 256;   // defaults: fastest shape of a sweep on GB300
+    int G = 4, threads = 128, jtile = 256;   // set per precision by nb_ensemble_init
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     double graph_t_end = -1.0;
@@ -1279,7 +1279,10 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
     e->eps = eps;
     e->nc = n_systems;
     e->P = padded;
-    e->jtile = cf.precision == NB_MIXED ? 1024 : 512;  // FP64 and EX: 512
+    // defaults from shape sweeps on GB300: mixed 4 x 128 threads, j-tile
+    // 1024; FP64 and EX (evaluation-heavy steps) 8 x 128, j-tile 512
+    e->jtile = cf.precision == NB_MIXED ? 1024 : 512;
+    e->G = cf.precision == NB_MIXED ? 4 : 8;
     auto bail = [&](nb_status s) {
         nb_set_thread_error(e->err.c_str());
         ens_free_all(e);

@@ -683,7 +683,8 @@ def adjoint_bench(args):
 
 
 def integrate_bench(args):
-    """Plummer N = 65536, FP64 throughout: one full-N evaluation (2^32
+    """Plummer N = 65536 (--prec fp64 by default in this mode's reference
+    config; ex and mixed also run): one full-N evaluation (2^32
     interactions), then block-step integration to t = 1/16 through
     nb_run_until (active sets from 1 to N particles)."""
     import numpy as np
@@ -693,7 +694,7 @@ def integrate_bench(args):
     import paper_1901_08532_gb300 as nb
     torch.cuda.set_device(0)
     n = args.n if args.n != N_BODY else 65536
-    prec = nb.NB_MIXED if args.prec == "mixed" else nb.NB_FP64
+    prec = {"mixed": nb.NB_MIXED, "fp64": nb.NB_FP64, "ex": nb.NB_EX, "sp": nb.NB_SP}[args.prec]
     m, x, v = ni.plummer(n, 2)
     stream = torch.cuda.current_stream()
     # dt_max = 2^-4 so that every particle synchronises at t_end = 1/16
@@ -718,11 +719,14 @@ def integrate_bench(args):
     hist = np.bincount(np.floor(np.log2(np.maximum(ln, 1))).astype(int))
     flops = FLOPS_PER_INTERACTION * float(n) * n / full_s / 1e12
     peak = PEAK_FP64_TFLOPS if prec == nb.NB_FP64 else PEAK_FP32_TFLOPS
+    n_fp32_ops = {nb.NB_EX: EX_OPS_PER_INTERACTION}.get(prec)
     print(json.dumps({"workload": f"plummer_N{n}_eps1e-4_{args.prec}", "full_eval_s": full_s,
                       "full_eval_interactions_per_s": float(n) * n / full_s,
-                      "full_eval_frac_of_peak": flops / peak,
+                      "full_eval_frac_of_peak": (flops / peak if n_fp32_ops is None else
+                                                 n_fp32_ops * float(n) * n / full_s / PEAK_FP32_OPS),
                       "integration_t_end": 1.0 / 16, "block_steps": steps,
-                      "integration_s": el, "integration_interactions": i1 - i0,
+                      "integration_s": el, "us_per_block_step": 1e6 * el / max(steps, 1),
+                      "integration_interactions": i1 - i0,
                       "integration_interactions_per_s": (i1 - i0) / el,
                       "mean_active": float(ln.mean()), "max_active": int(ln.max()),
                       "active_log2_histogram": hist.tolist(), "energy_rel_error": abs((E1 - E0) / E0)}))

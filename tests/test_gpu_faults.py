@@ -10,7 +10,7 @@ from nbhelp import nb_gpu, rel_err
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 3])
 def test_timed_out_wait_reports_etimeout_and_context_recovers(prec):
     nb = nb_gpu()
     n = 2048

@@ -9,7 +9,8 @@
 //   schedule  t_next = min(t_i + dt_i) over the system; active set in
 //             ascending order (each CTA scans its slice once, the minima and
 //             counts meet through distributed shared memory);
-//   predict   each CTA its slice, into the system's evaluation buffer;
+//   predict   each CTA its slice: for small active sets straight into
+//             shared memory, otherwise into the system's evaluation buffer;
 //   evaluate  small active sets (<= kSmall): every CTA evaluates the whole
 //             set against its own slice and the owner of each active
 //             particle adds the CTAs' partial sums in rank order (two cluster
@@ -17,6 +18,9 @@
 //             active particles against all of the system's particles, j-tiles
 //             by TMA bulk copy into shared memory;
 //   correct   the owner (small sets) or the evaluating CTA (larger sets).
+// Precisions (kernel template PR): FP64 (0); mixed (1), whose predictor and
+// corrector run from an FP32 copy of the state; EX double words (2) with the
+// FP64 predictor and corrector.
 // Phases are separated by the cluster barrier (a hardware barrier with
 // release/acquire semantics at cluster scope, no flag spinning).  Systems are
 // independent, so no grid-wide synchronisation exists.  The only waits that

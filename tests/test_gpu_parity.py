@@ -229,9 +229,11 @@ def test_tiny_systems(n, prec):
     g = nb.NBody(m, x, v, 1e-3, precision=prec)
     ref = O.System(m, x, v, 1e-3)
     st_g, st_r = g.state(), ref.state()
-    rtol = {0: 1e-12, 1: 1e-5, 3: 1e-10}[prec]
     for k in ("a", "j", "s"):
-        np.testing.assert_allclose(st_g[k], st_r[k], rtol=rtol, atol=1e-300)
+        if prec == 1:   # FP32 pair arithmetic: per-particle error over the vector norm
+            assert rel_err(st_g[k], st_r[k]).max() < 1e-5, k
+        else:
+            np.testing.assert_allclose(st_g[k], st_r[k], rtol={0: 1e-12, 3: 1e-10}[prec], atol=1e-300)
     if prec == 1 and not np.array_equal(st_g["dt"], st_r["dt"]):
         # FP32 rounding moved a starting step across a power of two: another
         # valid trajectory; the steps may differ by one factor of two only

@@ -89,6 +89,9 @@ def parse():
     p.add_argument("--ens-sample", type=int, default=8,
                    help="systems in the one-at-a-time comparison (0: skip)")
     p.add_argument("--ens-cmp-t-end", type=float, default=0.125)
+    p.add_argument("--ens-tune", action="store_true",
+                   help="pick the launch shape with the autotuner (candidate shapes timed on a "
+                        "32-system sample to t = 1/8) instead of --ens-shapes")
     p.add_argument("--integrate", action="store_true",
                    help="Plummer N=65536 (equal masses, eps 1e-4, seed 2), FP64: one full-N "
                         "evaluation, then block steps to t = 1/16; interactions/s and the "
@@ -613,6 +616,22 @@ def ensemble_bench(args):
         prec = prec_of[prec_name]
         res = {"t_end": args.ens_t_end, "shapes": {}}
         shapes = shapes_for(prec_name)
+        if args.ens_tune:
+            from paper_1901_08532_gb300.autotune import tune_ensemble
+            order = np.argsort(sizes)
+            pick = [int(order[q]) for q in np.linspace(0, sizes.size - 1, 32).astype(int)]
+            jts = (512, 1024) if prec_name == "mixed" else (256, 512)
+            cands = [(g, thr, jt) for g in (2, 4, 8) for thr in (64, 128) for jt in jts]
+
+            def make(pick=pick, prec=prec):
+                return nb.Ensemble(sizes[pick], *cat(pick), EPS, precision=prec)
+
+            def log(rec, prec_name=prec_name):
+                print(json.dumps({"tune": prec_name, **rec}), flush=True)
+
+            best, _ = tune_ensemble(make, 0.125, cands, log)
+            shapes = [best]
+            res["tuned_on"] = {"systems": len(pick), "t_end": 0.125, "candidates": len(cands)}
         for sh in shapes:
             r = run_ens(everyone, prec, sh, args.ens_t_end)
             res["shapes"]["%dx%dx%d" % sh] = r

@@ -7,6 +7,10 @@ shape) through the C-ABI (nb_set_tiles + nb_evaluate, CUDA events on the
 context's stream) and keeps the fastest.  Results are cached per
 (precision, n, n_act bucket) in memory and, optionally, in a JSON file.
 
+Ensembles: tune_ensemble() times candidate cluster shapes (blocks per
+system, threads, j-tile) on fresh copies of an ensemble and keeps the one
+with the highest interaction rate.
+
 Command line (prints one JSON line per timed shape, then the best):
     python -m paper_1901_08532_gb300.autotune --n 1048576 --n-act 1024 --prec mixed
 """
@@ -95,6 +99,57 @@ def tune(ctx, active, reps=3, log=None, cache_file=None):
         data[json.dumps(list(key))] = {"shape": best[0], "seconds": best[1]}
         with open(cache_file, "w") as f:
             json.dump(data, f, indent=1)
+    return best
+
+
+ENSEMBLE_SPACE = {"ctas_per_system": (2, 4, 8), "threads": (64, 128, 256), "jtile": (256, 512, 1024)}
+
+
+def ensemble_candidates(precision: int):
+    """Ensemble launch shapes worth timing (blocks per system, threads per
+    block, j-tile), the library's default for the precision first."""
+    default = (4, 128, 1024) if precision == 1 else (8, 128, 512)
+    yield default
+    for g in ENSEMBLE_SPACE["ctas_per_system"]:
+        for thr in ENSEMBLE_SPACE["threads"]:
+            for jt in ENSEMBLE_SPACE["jtile"]:
+                if (g, thr, jt) != default:
+                    yield (g, thr, jt)
+
+
+def tune_ensemble(make, t_probe, shapes=None, log=None):
+    """Pick the fastest ensemble launch shape.
+
+    make() must return a fresh Ensemble of the workload (each candidate runs
+    on its own copy, because a run advances the state); every candidate is
+    run to t_probe and timed on the host around Ensemble.run, which
+    synchronises.  The score is interactions per second, so that shapes whose
+    rounding leads to different (equally valid) trajectories compare fairly.
+    Returns (shape, interactions_per_s)."""
+    import time
+    best = (None, 0.0)
+    for shape in (shapes or ensemble_candidates(make().precision)):
+        ens = make()
+        try:
+            ens.set_shape(*shape)
+        except Exception:  # the library rejects shapes that do not fit
+            ens.close()
+            continue
+        _, it0, _ = ens.stats()
+        t0 = time.perf_counter()
+        try:
+            ens.run(t_probe)
+        except Exception:
+            ens.close()
+            continue
+        el = time.perf_counter() - t0
+        _, it1, _ = ens.stats()
+        ens.close()
+        rate = (it1 - it0) / el if el > 0 else 0.0
+        if log is not None:
+            log({"shape": shape, "seconds": el, "interactions_per_s": rate})
+        if rate > best[1]:
+            best = (shape, rate)
     return best
 
 

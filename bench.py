@@ -608,7 +608,7 @@ def ensemble_bench(args):
     precs = ("mixed", "fp64") if args.prec == "both" else (args.prec,)
     prec_of = {"mixed": nb.NB_MIXED, "fp64": nb.NB_FP64, "ex": nb.NB_EX}
     def shapes_for(prec_name):
-        spec = args.ens_shapes or ("4x128" if prec_name == "mixed" else "8x128")
+        spec = args.ens_shapes or ("4x128" if prec_name == "mixed" else "8x128x256")
         out = [tuple(int(q) for q in sh.split("x")) for sh in spec.split(",")]
         return [sh if len(sh) == 3 else (sh[0], sh[1], 0) for sh in out]
     everyone = list(range(sizes.size))
@@ -621,7 +621,7 @@ def ensemble_bench(args):
             order = np.argsort(sizes)
             pick = [int(order[q]) for q in np.linspace(0, sizes.size - 1, 32).astype(int)]
             jts = (512, 1024) if prec_name == "mixed" else (256, 512)
-            cands = [(g, thr, jt) for g in (2, 4, 8) for thr in (64, 128) for jt in jts]
+            cands = [(g, thr, jt) for g in (2, 4, 8, 16) for thr in (64, 128) for jt in jts]
 
             def make(pick=pick, prec=prec):
                 return nb.Ensemble(sizes[pick], *cat(pick), EPS, precision=prec)

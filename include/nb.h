@@ -263,10 +263,12 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
                            const double *m, const double *x, const double *v, double eps,
                            const nb_config *cfg);
 
-/* Launch shape: thread blocks per system (1..8, one hardware cluster),
+/* Launch shape: thread blocks per system (1..16, one hardware cluster; above
+ * 8 the non-portable cluster size, NB_EINVAL from nb_ensemble_run where the
+ * device cannot co-schedule it),
  * threads per block (64..256, multiple of 32), j-tile length (multiple of 4).
  * Defaults: NB_MIXED 4 blocks of 128 threads, j-tile 1024; NB_FP64 and NB_EX
- * 8 blocks of 128 threads, j-tile 512. */
+ * 8 blocks of 128 threads, j-tile 256. */
 nb_status nb_ensemble_set_shape(nb_ensemble *e, int32_t ctas_per_system, int32_t threads,
                                 int32_t jtile);
 

@@ -376,7 +376,7 @@ class Ensemble:
         if ctas_per_system is None:
             ctas_per_system = 4 if self.precision == NB_MIXED else 8
         if jtile is None:
-            jtile = 1024 if self.precision == NB_MIXED else 512
+            jtile = 1024 if self.precision == NB_MIXED else 256
         self._check(_lib.nb_ensemble_set_shape(self._e, int(ctas_per_system), int(threads), int(jtile)))
 
     def run(self, t_end, use_graph=True):

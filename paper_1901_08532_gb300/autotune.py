@@ -102,13 +102,13 @@ def tune(ctx, active, reps=3, log=None, cache_file=None):
     return best
 
 
-ENSEMBLE_SPACE = {"ctas_per_system": (2, 4, 8), "threads": (64, 128, 256), "jtile": (256, 512, 1024)}
+ENSEMBLE_SPACE = {"ctas_per_system": (2, 4, 8, 16), "threads": (64, 128, 256), "jtile": (256, 512, 1024)}
 
 
 def ensemble_candidates(precision: int):
     """Ensemble launch shapes worth timing (blocks per system, threads per
     block, j-tile), the library's default for the precision first."""
-    default = (4, 128, 1024) if precision == 1 else (8, 128, 512)
+    default = (4, 128, 1024) if precision == 1 else (8, 128, 256)
     yield default
     for g in ENSEMBLE_SPACE["ctas_per_system"]:
         for thr in ENSEMBLE_SPACE["threads"]:

@@ -48,4 +48,4 @@ def test_ensemble_candidates_start_with_the_default():
     autotune = pytest.importorskip("paper_1901_08532_gb300.autotune")
     assert next(iter(autotune.ensemble_candidates(1))) == (4, 128, 1024)
     ex = list(autotune.ensemble_candidates(3))
-    assert ex[0] == (8, 128, 512) and len(ex) == len(set(ex)) == 27
+    assert ex[0] == (8, 128, 256) and len(ex) == len(set(ex)) == 36

@@ -113,7 +113,7 @@ def test_ex_ensemble_launch_shapes_agree_and_track_fp64():
     nb = nb_gpu()
     ms, xs, vs = _systems(SIZES, 70)
     out = []
-    for g, thr in ((1, 128), (4, 128), (8, 64)):
+    for g, thr in ((1, 128), (4, 128), (8, 64), (16, 64)):   # 16: non-portable cluster size
         ens = nb.Ensemble(SIZES, *_concat(ms, xs, vs), 1e-4, precision=nb.NB_EX, dt_max=2.0 ** -5)
         ens.set_shape(g, thr)
         ens.run(2.0 ** -5)

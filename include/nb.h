@@ -57,14 +57,16 @@ typedef enum {
     NB_ESTATE = -6      /* call out of order (e.g. correct before eval)   */
 } nb_status;
 
-/* Arithmetic of the evaluation step (section 3 item 6).  Prediction,
- * correction, time steps and energy are FP64 in both modes. */
+/* Arithmetic of the evaluation step (section 3 item 6).  In a context
+ * (nb_init) prediction, correction, time steps and energy are FP64 in every
+ * mode; ensembles differ for NB_MIXED (see nb_ensemble_init). */
 typedef enum {
     NB_FP64 = 0,  /* every operation of the pair sum in IEEE double          */
     NB_MIXED = 1, /* FP64 positions and accumulation; pair differences
                      rounded to FP32 (positions as hi + lo FP32 pairs), FP32
-                     rsqrt and pair arithmetic, FP32 sums within a j-tile
-                     folded into a compensated (TwoSum) accumulator         */
+                     pair arithmetic with R^(-1/2) and 1/R from the special-
+                     function unit, FP32 sums within a j-tile folded into a
+                     compensated (TwoSum) accumulator                       */
     NB_SP = 2,    /* single precision control (section 3 item 6): as NB_MIXED
                      but positions rounded to FP32 (no lo part), so pair
                      differences carry the rounding of the positions; not
@@ -107,10 +109,15 @@ typedef struct {
                           the caller supplies them with nb_set_state
                           (checkpoint resume, benchmarks)                     */
     void *stream;      /* cudaStream_t for all work; NULL = legacy default    */
+    int32_t device_steps; /* 1: nb_run_until runs block steps whose active set
+                          holds at most 64 particles inside one cooperative
+                          launch (device-resident scheduling, evaluation and
+                          correction; larger steps return to the host-driven
+                          path); 0: every step host-driven                   */
 } nb_config;
 
 /* Fill cfg with the defaults listed above (FP64, automatic tiles,
- * start_forces = 1). */
+ * start_forces = 1, device_steps = 1). */
 void nb_config_default(nb_config *cfg);
 
 /* Create a context on the current CUDA device for n particles with masses

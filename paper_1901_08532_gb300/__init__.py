@@ -51,7 +51,8 @@ class Tiles(C.Structure):
 class Config(C.Structure):
     _fields_ = [("precision", C.c_int32), ("eta", C.c_double), ("eta_s", C.c_double),
                 ("dt_min", C.c_double), ("dt_max", C.c_double), ("dt_shared", C.c_double),
-                ("tiles", Tiles), ("start_forces", C.c_int32), ("stream", C.c_void_p)]
+                ("tiles", Tiles), ("start_forces", C.c_int32), ("stream", C.c_void_p),
+                ("device_steps", C.c_int32)]
 
 
 _d = C.POINTER(C.c_double)
@@ -156,12 +157,14 @@ class NBody:
 
     m[n], x[n,3], v[n,3] are host arrays (copied); eps > 0.  precision is
     NB_FP64, NB_MIXED, NB_SP or NB_EX (NB_SP NBody only).  stream: a torch.cuda.Stream or raw cudaStream_t
-    (default: torch's current stream).
+    (default: torch's current stream).  device_steps: run_until / run_diag run
+    block steps with at most 64 active particles in the device-resident
+    stepper (one cooperative launch per run of such steps).
     """
 
     def __init__(self, m, x, v, eps, precision=NB_FP64, eta=0.4, eta_s=0.01,
                  dt_min=2.0 ** -20, dt_max=2.0 ** -3, dt_shared=0.0, tiles=None, stream=None,
-                 start_forces=True):
+                 start_forces=True, device_steps=True):
         m = _f64(m)
         n = m.size
         x, v = _f64(x, (n, 3)), _f64(v, (n, 3))
@@ -173,6 +176,7 @@ class NBody:
             for k, val in dict(tiles).items():
                 setattr(cfg.tiles, k, int(val))
         cfg.start_forces = 1 if start_forces else 0
+        cfg.device_steps = 1 if device_steps else 0
         cfg.stream = _stream_handle(stream)
         self.n = n
         self.precision = precision

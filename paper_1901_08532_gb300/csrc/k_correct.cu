@@ -8,6 +8,7 @@
 //     eta (A1 / A4)^(1/3), A_k = sqrt(|a^(k-1)| |a^(k+1)|) + |a^(k)|,
 //     rounded down to a power of two, clamped to [dt_min, dt_max], at most
 //     doubled, and doubled only where t1 is a multiple of the doubled step.
+#include "nb_correct.cuh"
 #include "nb_device.cuh"
 #include "nb_internal.cuh"
 
@@ -33,54 +34,12 @@ __global__ void __launch_bounds__(128) correct_kernel(CorrectArgs a)
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.n_act)
         return;
-    const size_t N = static_cast<size_t>(a.n);
-    const int i = a.act[k];
-    const double h = a.t1 - a.t[i];
-    const double ih = 1.0 / h;  // exact: h is a sum of powers of two equal to dt_i
-    double n2[6] = {0, 0, 0, 0, 0, 0};  // squared norms of a1, j1, s1, c1, d1, e1
-    bool finite = true;
+    double f[9];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        double *px = a.st + (F_X * 3 + d) * N + i;
-        double *pv = a.st + (F_V * 3 + d) * N + i;
-        double *pa = a.st + (F_A * 3 + d) * N + i;
-        double *pj = a.st + (F_J * 3 + d) * N + i;
-        double *ps = a.st + (F_S * 3 + d) * N + i;
-        double *pc = a.st + (F_C * 3 + d) * N + i;
-        const double a0 = *pa, j0 = *pj, s0 = *ps;
-        const double a1 = a.anew[(0 + d) * (size_t)a.ostride + k];
-        const double j1 = a.anew[(3 + d) * (size_t)a.ostride + k];
-        const double s1 = a.anew[(6 + d) * (size_t)a.ostride + k];
-        const nbk::Corrected r = nbk::hermite_correct(h, ih, *px, *pv, a0, j0, s0, a1, j1, s1);
-        const double x1 = r.x1, v1 = r.v1, c1 = r.c1, d1 = r.d1, e1 = r.e1;
-        finite = finite && isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1) &&
-                 isfinite(s1) && isfinite(c1);
-        *px = x1;
-        *pv = v1;
-        *pa = a1;
-        *pj = j1;
-        *ps = s1;
-        *pc = c1;
-        n2[0] = fma(a1, a1, n2[0]);
-        n2[1] = fma(j1, j1, n2[1]);
-        n2[2] = fma(s1, s1, n2[2]);
-        n2[3] = fma(c1, c1, n2[3]);
-        n2[4] = fma(d1, d1, n2[4]);
-        n2[5] = fma(e1, e1, n2[5]);
-    }
-    a.t[i] = a.t1;
-    double dtn;
-    bool hit = false;
-    if (a.dt_shared > 0.0) {
-        dtn = a.dt_shared;
-    } else {
-        dtn = quantise(nbk::aarseth_dt(n2, a.eta), a.dt[i], a.t1, a.dt_min, a.dt_max, &hit);
-    }
-    a.dt[i] = dtn;
-    if (hit)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->floor_hits), 1ull);
-    if (!finite)
-        atomicOr(&a.ctl->err, NB_ERR_NONFINITE);
+    for (int q = 0; q < 9; ++q)
+        f[q] = a.anew[q * (size_t)a.ostride + k];
+    nbk::correct_particle_fp64(a.st, a.t, a.dt, static_cast<size_t>(a.n), a.act[k], a.t1, f, a.eta,
+                               a.dt_min, a.dt_max, a.dt_shared, a.ctl);
 }
 
 // Start-up (nb_init): pass 0 stores a and jerk of the first evaluation (made

@@ -163,6 +163,89 @@ nb_status schedule(nb_ctx *c, double *tn, int64_t *n_act)
     return NB_OK;
 }
 
+// Block steps until the next block time passes t_end; steps with small
+// active sets run in the device-resident stepper (one cooperative launch for
+// a whole run of them), a step with a larger set runs here through the tuned
+// kernels.  Shared steps make every particle active, so they always take the
+// host path.  Appends to the step log (log_t, log_n, capacity log_cap) and
+// counts into *steps.
+nb_status integrate_to(nb_ctx *c, double t_end, int64_t log_cap, double *log_t, int64_t *log_n,
+                       int64_t *steps_io)
+{
+    const bool device = c->cfg.device_steps != 0 && c->cfg.dt_shared == 0.0;
+    int64_t steps = *steps_io;
+    if (device && log_cap > steps) {
+        CU(c, cudaMalloc(&c->stp_log_t, static_cast<size_t>(log_cap) * sizeof(double)));
+        CU(c, cudaMalloc(&c->stp_log_n, static_cast<size_t>(log_cap) * sizeof(int64_t)));
+    }
+    auto release_log = [&]() {
+        cudaFree(c->stp_log_t);
+        cudaFree(c->stp_log_n);
+        c->stp_log_t = nullptr;
+        c->stp_log_n = nullptr;
+    };
+    nb_status s = NB_OK;
+    for (;;) {
+        if (device) {
+            int64_t ds = 0, acts = 0;
+            int reason = 0, na_last = 0;
+            double t_last = 0.0;
+            cudaError_t e = nb_run_stepper(c, t_end, log_cap, steps, &ds, &acts, &reason, &na_last, &t_last);
+            if (e != cudaSuccess) {
+                release_log();
+                return cuda_fail(c, e, "device-resident block steps");
+            }
+            if (ds > 0) {
+                if (log_cap > steps) {
+                    const int64_t k = std::min(ds, log_cap - steps);
+                    e = cudaMemcpyAsync(log_t + steps, c->stp_log_t + steps, k * sizeof(double),
+                                        cudaMemcpyDeviceToHost, c->stream);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(log_n + steps, c->stp_log_n + steps, k * sizeof(int64_t),
+                                            cudaMemcpyDeviceToHost, c->stream);
+                    if (e == cudaSuccess)
+                        e = cudaStreamSynchronize(c->stream);
+                    if (e != cudaSuccess) {
+                        release_log();
+                        return cuda_fail(c, e, "step log copy");
+                    }
+                }
+                steps += ds;
+                c->t_sys = t_last;
+                c->n_act = na_last;
+                c->interactions += static_cast<double>(acts) * static_cast<double>(c->n);
+            }
+            if (reason != 1)
+                break;  // t_end reached, or an error flag (reported by sync_ctl)
+        }
+        double tn;
+        int64_t na;
+        s = schedule(c, &tn, &na);
+        if (s != NB_OK)
+            break;
+        if (tn > t_end)
+            break;
+        if (na < 1) {
+            s = fail(c, NB_ESTATE, "scheduler found no active particle");
+            break;
+        }
+        s = advance(c, tn, na);
+        if (s != NB_OK)
+            break;
+        c->t_sys = tn;
+        if (steps < log_cap) {
+            log_t[steps] = tn;
+            log_n[steps] = na;
+        }
+        ++steps;
+    }
+    release_log();
+    c->have_pred = false;
+    c->have_eval = false;
+    *steps_io = steps;
+    return s;
+}
+
 void free_all(nb_ctx *c)
 {
     cudaFree(c->m);
@@ -181,6 +264,13 @@ void free_all(nb_ctx *c)
     cudaFree(c->ctl);
     cudaFree(c->diag);
     cudaFree(c->ring);
+    cudaFree(c->stp_bmin);
+    cudaFree(c->stp_bcnt);
+    cudaFree(c->stp_cand);
+    cudaFree(c->stp_part);
+    cudaFree(c->stp_out);
+    if (c->stp_out_h)
+        cudaFreeHost(c->stp_out_h);
     if (c->ctl_h)
         cudaFreeHost(c->ctl_h);
     if (c->diag_h)
@@ -209,6 +299,7 @@ void nb_config_default(nb_config *cfg)
     cfg->dt_shared = 0.0;
     cfg->start_forces = 1;
     cfg->stream = nullptr;
+    cfg->device_steps = 1;
 }
 
 nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x, const double *v,
@@ -492,26 +583,9 @@ nb_status nb_run_until(nb_ctx *c, double t_end, int64_t *steps_out, int64_t log_
     if (log_cap > 0 && (!log_t || !log_n))
         return fail(c, NB_EINVAL, "log buffers must not be NULL when log_cap > 0");
     int64_t steps = 0;
-    for (;;) {
-        double tn;
-        int64_t na;
-        nb_status s = schedule(c, &tn, &na);
-        if (s != NB_OK)
-            return s;
-        if (tn > t_end)
-            break;
-        if (na < 1)
-            return fail(c, NB_ESTATE, "scheduler found no active particle");
-        s = advance(c, tn, na);
-        if (s != NB_OK)
-            return s;
-        c->t_sys = tn;
-        if (steps < log_cap) {
-            log_t[steps] = tn;
-            log_n[steps] = na;
-        }
-        ++steps;
-    }
+    nb_status s = integrate_to(c, t_end, log_cap, log_t, log_n, &steps);
+    if (s != NB_OK)
+        return s;
     if (steps_out)
         *steps_out = steps;
     return sync_ctl(c);
@@ -564,22 +638,12 @@ nb_status nb_run_diag(nb_ctx *c, double t_end, double dt_diag, int64_t cap, doub
         return s;
     double t_next = c->t_sys + dt_diag;
     while (t_next <= t_end) {
-        for (;;) {
-            double tn;
-            int64_t na;
-            s = schedule(c, &tn, &na);
-            if (s != NB_OK)
-                return s;
-            if (tn > t_next)
-                break;
-            if (na < 1)
-                return fail(c, NB_ESTATE, "scheduler found no active particle");
-            s = advance(c, tn, na);
-            if (s != NB_OK)
-                return s;
-            c->t_sys = tn;
-            ++steps;
-        }
+        s = integrate_to(c, t_next, 0, nullptr, nullptr, &steps);
+        if (s != NB_OK)
+            return s;
+        s = sync_ctl(c);  // an error flag ends the run before the sample
+        if (s != NB_OK)
+            return s;
         s = sample(t_next);
         if (s != NB_OK)
             return s;

@@ -72,6 +72,13 @@ struct nb_ctx {
     double *diag_h = nullptr;  // [8] pinned host mirror
     double *ring = nullptr;    // [ring_cap][8] diagnostics samples of nb_run_diag
     int64_t ring_cap = 0;
+    // device-resident stepper (k_stepper.cu): per-block scratch, results, log
+    double *stp_bmin = nullptr;
+    int *stp_bcnt = nullptr, *stp_cand = nullptr;
+    double *stp_part = nullptr;
+    void *stp_out = nullptr, *stp_out_h = nullptr;
+    double *stp_log_t = nullptr;
+    int64_t *stp_log_n = nullptr;
 
     int64_t n_act = 0;         // size of the last evaluated set
     bool have_pred = false;
@@ -222,6 +229,11 @@ cudaError_t nb_launch_schedule(nb_ctx *c);
 cudaError_t nb_launch_iota(nb_ctx *c, int n);
 // nb_api.cu: message returned by nb_last_error(NULL) on this thread
 void nb_set_thread_error(const char *msg);
+// k_stepper.cu
+int nb_stepper_small();
+cudaError_t nb_run_stepper(nb_ctx *c, double t_end, int64_t log_cap, int64_t log_base, int64_t *steps,
+                           int64_t *act_sum, int *reason, int *n_act, double *t_last);
+
 // k_energy.cu
 cudaError_t nb_launch_energy(nb_ctx *c, double *ek_pe_dev);
 cudaError_t nb_launch_angmom(nb_ctx *c, double *l4_dev);

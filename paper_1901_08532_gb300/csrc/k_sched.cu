@@ -138,14 +138,14 @@ cudaError_t nb_launch_schedule(nb_ctx *c)
     tmin_kernel<<<g1, kThreads, 0, c->stream>>>(c->t, c->dt, n, c->ctl);
     const int nb = (n + kPerBlock - 1) / kPerBlock;
     count_kernel<<<nb, kThreads, 0, c->stream>>>(c->t, c->dt, n, c->ctl, c->blk);
-    compact_kernel<<<nb, kThreads, 0, c->stream>>>(c->t, c->dt, n, c->ctl, c->blk, c->act);
+    compact_kernel<<<nb, kThreads, 0, c->stream>>>(c->t, c->dt, n, c->ctl, c->blk, c->act_next);
     c->launches += 3;
     return cudaGetLastError();
 }
 
-cudaError_t nb_launch_iota(nb_ctx *c, int n)
+cudaError_t nb_launch_iota(nb_ctx *c, int n, int32_t *dst)
 {
-    iota_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(c->act, n);
+    iota_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(dst, n);
     c->launches += 1;
     return cudaGetLastError();
 }

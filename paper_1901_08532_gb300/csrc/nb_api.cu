@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "nb_internal.cuh"
@@ -128,9 +129,11 @@ nb_status eval_on_device(nb_ctx *c, const int32_t *act_dev, int64_t n_act)
     return NB_OK;
 }
 
-// predict -> evaluate -> correct for the active list in c->act.
+// predict -> evaluate -> correct for the active list the scheduler left in
+// c->act_next, which becomes c->act (the last step's set, for nb_get_active).
 nb_status advance(nb_ctx *c, double tn, int64_t n_act)
 {
+    std::swap(c->act, c->act_next);
     CU(c, nb_launch_predict(c, tn));
     nb_status s = eval_on_device(c, c->act, n_act);
     if (s != NB_OK)
@@ -142,13 +145,13 @@ nb_status advance(nb_ctx *c, double tn, int64_t n_act)
     return NB_OK;
 }
 
-// Next block time and active set (into c->act); returns status.
+// Next block time and active set (into c->act_next); returns status.
 nb_status schedule(nb_ctx *c, double *tn, int64_t *n_act)
 {
     if (c->cfg.dt_shared > 0.0) {
         *tn = c->t_sys + c->cfg.dt_shared;
         *n_act = c->n;
-        CU(c, nb_launch_iota(c, static_cast<int>(c->n)));
+        CU(c, nb_launch_iota(c, static_cast<int>(c->n), c->act_next));
         return NB_OK;
     }
     CU(c, nb_launch_schedule(c));
@@ -255,6 +258,7 @@ void free_all(nb_ctx *c)
     cudaFree(c->jb64);
     cudaFree(c->jf32);
     cudaFree(c->act);
+    cudaFree(c->act_next);
     cudaFree(c->anew);
     cudaFree(c->stage);
     cudaFree(c->part);
@@ -384,6 +388,7 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x, con
     } else
         CUI(cudaMalloc(&c->jb64, 5 * N * sizeof(double2)));
     CUI(cudaMalloc(&c->act, N * sizeof(int32_t)));
+    CUI(cudaMalloc(&c->act_next, N * sizeof(int32_t)));
     CUI(cudaMalloc(&c->anew, 9 * N * sizeof(double)));
     CUI(cudaMalloc(&c->stage, 3 * N * sizeof(double)));
     CUI(cudaMalloc(&c->blk, ((N + 1023) / 1024 + 1) * sizeof(int32_t)));
@@ -406,7 +411,7 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x, con
     CUI(cudaMemsetAsync(c->ctl, 0, sizeof(nb_ctl), c->stream));
 
     // start-up: pass 0 (a_j = 0) gives a and jerk, pass 1 gives snap
-    CUI(nb_launch_iota(c, static_cast<int>(n)));
+    CUI(nb_launch_iota(c, static_cast<int>(n), c->act));
     if (!cf.start_forces) {
         std::vector<double> d(N, cf.dt_shared > 0.0 ? cf.dt_shared : cf.dt_max);
         CUI(cudaMemcpyAsync(c->dt, d.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -506,7 +511,7 @@ nb_status nb_evaluate(nb_ctx *c, const int32_t *active, int64_t n_act, int activ
                 return fail(c, NB_EINVAL, "active index out of range");
     if (n_act > 0) {
         if (!active)
-            CU(c, nb_launch_iota(c, static_cast<int>(c->n)));
+            CU(c, nb_launch_iota(c, static_cast<int>(c->n), c->act));
         else if (active != c->act)
             CU(c, cudaMemcpyAsync(c->act, active, static_cast<size_t>(n_act) * sizeof(int32_t),
                                   active_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,

@@ -56,7 +56,8 @@ struct nb_ctx {
     double2 *jb64 = nullptr;   // [5][n]
     float *jf32 = nullptr;     // [13][npad]
     int64_t npad = 0;
-    int32_t *act = nullptr;    // [n]
+    int32_t *act = nullptr;    // [n] active set of the last step evaluated
+    int32_t *act_next = nullptr;  // [n] active set found by the scheduler, swapped in by the step
     double *anew = nullptr;    // [9][n]
     double *stage = nullptr;   // [3][n][3] output staging
     double *part = nullptr;    // split-j partials
@@ -226,7 +227,7 @@ cudaError_t nb_launch_rows_to_soa(nb_ctx *c, const double *rows, int field);
 cudaError_t nb_launch_soa_to_rows(nb_ctx *c, int field, double *rows);
 // k_sched.cu
 cudaError_t nb_launch_schedule(nb_ctx *c);
-cudaError_t nb_launch_iota(nb_ctx *c, int n);
+cudaError_t nb_launch_iota(nb_ctx *c, int n, int32_t *dst);
 // nb_api.cu: message returned by nb_last_error(NULL) on this thread
 void nb_set_thread_error(const char *msg);
 // k_stepper.cu

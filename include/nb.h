@@ -109,11 +109,13 @@ typedef struct {
                           the caller supplies them with nb_set_state
                           (checkpoint resume, benchmarks)                     */
     void *stream;      /* cudaStream_t for all work; NULL = legacy default    */
-    int32_t device_steps; /* 1: nb_run_until runs block steps whose active set
-                          holds at most 64 particles inside one cooperative
-                          launch (device-resident scheduling, evaluation and
-                          correction; larger steps return to the host-driven
-                          path); 0: every step host-driven                   */
+    int32_t device_steps; /* 1: nb_run_until and nb_run_diag run block steps
+                          whose active set holds at most 128 particles inside
+                          one cooperative launch (device-resident scheduling,
+                          evaluation and correction; larger steps return to
+                          the host-driven path, and after a launch that took
+                          no step the host tries again only after 1, 3, 7 ...
+                          host steps); 0: every step host-driven            */
 } nb_config;
 
 /* Fill cfg with the defaults listed above (FP64, automatic tiles,

@@ -158,7 +158,7 @@ class NBody:
     m[n], x[n,3], v[n,3] are host arrays (copied); eps > 0.  precision is
     NB_FP64, NB_MIXED, NB_SP or NB_EX (NB_SP NBody only).  stream: a torch.cuda.Stream or raw cudaStream_t
     (default: torch's current stream).  device_steps: run_until / run_diag run
-    block steps with at most 64 active particles in the device-resident
+    block steps with at most 128 active particles in the device-resident
     stepper (one cooperative launch per run of such steps).
     """
 

@@ -39,7 +39,7 @@ namespace {
 using namespace nbk;
 
 constexpr int kStepThreads = 128;
-constexpr int kStepSmall = 64;   // active sets up to this size are stepped on the device
+constexpr int kStepSmall = 128;  // active sets up to this size are stepped on the device
 constexpr int kChunkCap = 1024;  // j-records per shared-memory chunk
 
 struct StepOut {

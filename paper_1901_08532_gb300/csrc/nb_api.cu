@@ -188,8 +188,11 @@ nb_status integrate_to(nb_ctx *c, double t_end, int64_t log_cap, double *log_t, 
         c->stp_log_n = nullptr;
     };
     nb_status s = NB_OK;
+    int backoff = 0, skip = 0;  // host steps before the stepper is tried again
     for (;;) {
-        if (device) {
+        if (device && skip > 0) {
+            --skip;
+        } else if (device) {
             int64_t ds = 0, acts = 0;
             int reason = 0, na_last = 0;
             double t_last = 0.0;
@@ -220,6 +223,10 @@ nb_status integrate_to(nb_ctx *c, double t_end, int64_t log_cap, double *log_t, 
             }
             if (reason != 1)
                 break;  // t_end reached, or an error flag (reported by sync_ctl)
+            // the next active set is too large: a launch that took no step at
+            // all doubles the number of host steps before the next attempt
+            backoff = ds > 0 ? 0 : std::min(2 * backoff + 1, 255);
+            skip = backoff;
         }
         double tn;
         int64_t na;

@@ -15,8 +15,12 @@ region.  Secondary numbers: the FP64 kernel at active fraction 2^-5, the
 mixed kernel at active fractions 2^-10 and 2^-5 (split-j), and the mixed
 error against the FP64 GPU path.
 
---impl reference times the FP64 CPU oracle (the reference arm) on the
-host cores for the same workload, one bounded i-sample per step.
+The CPU leg runs the FP64 CPU oracle on the host cores: one core on 48
+sampled i-particles, then one instance per core on disjoint rows of a seeded
+4096-particle subset (all against the 2^20 j); the oracle's sums for that
+subset check both GPU paths (err_vs_oracle).  --impl reference times the
+oracle (the reference arm) on the host cores for the same workload, one
+bounded i-sample per step.
 """
 from __future__ import annotations
 
@@ -117,13 +121,14 @@ def _oracle_worker(args):
     (and, when asked, the sums and their condition numbers, untimed)."""
     lo, hi, n = args[:3]
     keep = len(args) > 3 and args[3]
+    sample = args[4] if len(args) > 4 else 4096
     import numpy as np
 
     import nb_inputs as ni
     import oracle as O
     m, x, v = ni.plummer(n, SEED, imf="salpeter")
     a = np.zeros_like(x)
-    act = ni.active_subset(n, 4096, 31)[lo:hi]
+    act = ni.active_subset(n, sample, 31)[lo:hi]
     t0 = time.perf_counter()
     sums = O.evaluate(m, x, v, a, EPS, act)
     sec = time.perf_counter() - t0
@@ -132,24 +137,33 @@ def _oracle_worker(args):
     return sec, act, sums, O.evaluate_kappa(m, x, v, a, EPS, act)
 
 
-def cpu_baseline(n, per_core_rows=48, want_seconds=None):
-    """Single-threaded FP64 oracle timed on (a) one core and (b) one
-    independent instance per usable core on disjoint i-rows of a seeded
-    4096-particle sample, each i against all n j."""
+def cpu_baseline(n, per_core_rows=48, sample=4096):
+    """Single-threaded FP64 oracle timed on (a) one core, per_core_rows
+    i-particles, and (b) one independent instance per usable core on
+    disjoint i-rows covering the whole seeded `sample`-particle subset, each i
+    against all n j.  The oracle's sums and condition numbers for the whole
+    subset are kept (untimed) for the accuracy check of the GPU paths."""
     import multiprocessing as mp
+
+    import numpy as np
     cores = len(os.sched_getaffinity(0))
-    t1, act, sums, kap = _oracle_worker((0, per_core_rows, n, True))
+    t1 = _oracle_worker((0, per_core_rows, n, False, sample))
     one = per_core_rows * n / t1
     ctx = mp.get_context("spawn")
-    k = min(cores, 4096 // per_core_rows)
-    jobs = [(r * per_core_rows, (r + 1) * per_core_rows, n) for r in range(k)]
+    k = max(1, min(cores, sample))
+    edges = [sample * r // k for r in range(k + 1)]
+    jobs = [(edges[r], edges[r + 1], n, True, sample) for r in range(k)]
     with ctx.Pool(k) as pool:
-        secs = pool.map(_oracle_worker, jobs)
-    allc = k * per_core_rows * n / max(secs)   # instances run concurrently
+        res = pool.map(_oracle_worker, jobs)
+    secs = [r[0] for r in res]
+    allc = sample * n / max(secs)   # instances run concurrently
+    act = np.concatenate([r[1] for r in res])
+    sums = tuple(np.concatenate([r[2][q] for r in res]) for q in range(3))
+    kap = tuple(np.concatenate([r[3][q] for r in res]) for q in range(3))
     return {"value": allc, "unit": "interactions/s", "cores": k, "kind": "oracle",
             "one_core": one, "_ref": (act, sums, kap),
-            "sample": f"{k} oracle instances x {per_core_rows} i-particles of a seeded 4096-i "
-                      f"subset x all {n} j (FP64, single-threaded C); one-core run: "
+            "sample": f"{k} oracle instances on disjoint i-rows of a seeded {sample}-i subset "
+                      f"x all {n} j (FP64, single-threaded C); one-core run: "
                       f"{per_core_rows} i x {n} j in {t1:.1f} s",
             "host_cpu": _cpu_model()}
 

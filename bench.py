@@ -58,6 +58,7 @@ PEAK_FP32_OPS = SM_COUNT * 128 * SM_MAX_MHZ * 1e6                 # 40.3e12 / s
 TRAFFIC = {"kernel_sha": "f48d47d3a8d9b0db", "bytes_per_launch": 119.15e6 + 69.61e6,
            "source": "profiles/eval_mixed_dram_plummer_N1048576_all_active.md"}
 WORKLOAD = "plummer_salpeter_N1048576_eps1e-4_shared_step_all_active"
+METRIC = "acc+jerk+snap interactions/s at N=2^20, mixed vs FP64 at rel err <= 1e-6"
 
 
 def _env_int(name, default):
@@ -192,12 +193,14 @@ def run_reference(args):
     for s in range(args.steps):
         times.append(_oracle_worker((s * rows % 4096, s * rows % 4096 + rows, n)))
     value = rows * n * len(times) / sum(times)
-    line = {"impl": "reference", "metric": "acc+jerk+snap interactions/s at N=2^20 (FP64 CPU oracle)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "interactions/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "eps": EPS, "seed": SEED,
+            "config": {"workload": WORKLOAD, "n": n, "eps": EPS, "seed": SEED, "imf": "salpeter",
+                       "arm": "FP64 CPU oracle (single-threaded C), the reference arm of a paper "
+                              "without code",
                        "step": f"oracle evaluation of {rows} sampled i x all {n} j"},
             "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": 1, "kind": "oracle",
                              "sample": f"{rows} i-particles of a seeded 4096-i subset x all {n} j per step"},
@@ -369,7 +372,7 @@ def run_ours(args):
         err_oracle = error_vs_oracle(nb, np, torch, m, x, v, stream, *cpu.pop("_ref"))
 
     line = {
-        "metric": "acc+jerk+snap interactions/s at N=2^20, mixed vs FP64 at rel err <= 1e-6",
+        "metric": METRIC,
         "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

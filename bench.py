@@ -90,7 +90,7 @@ def parse():
     p.add_argument("--ens-systems", type=int, default=256)
     p.add_argument("--ens-shapes", default="",
                    help="comma-separated ctas_per_system x threads [x jtile] shapes to time "
-                        "(default: 4x128 for mixed, 8x128 for fp64 and ex)")
+                        "(default 0x128x0: the library's default blocks and j-tile)")
     p.add_argument("--ens-sample", type=int, default=8,
                    help="systems in the one-at-a-time comparison (0: skip)")
     p.add_argument("--ens-cmp-t-end", type=float, default=0.125)
@@ -609,7 +609,8 @@ def ensemble_bench(args):
     def run_ens(idx, prec, shape, t_end):
         g, thr, jt = shape
         ens = nb.Ensemble(sizes[idx], *cat(idx), EPS, precision=prec)
-        ens.set_shape(g, thr, jt or None)
+        ens.set_shape(g or None, thr, jt or None)
+        used = ens.shape()
         _, it0, _ = ens.stats()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -617,7 +618,8 @@ def ensemble_bench(args):
         el = time.perf_counter() - t0
         steps, it1, launches = ens.stats()
         ens.close()
-        return {"seconds": el, "interactions": it1 - it0, "interactions_per_s": (it1 - it0) / el,
+        return {"shape_used": list(used), "seconds": el, "interactions": it1 - it0,
+                "interactions_per_s": (it1 - it0) / el,
                 "block_steps": int(steps.sum()), "max_steps": int(steps.max())}
 
     out = {"workload": f"ensemble_{args.ens_systems}_plummer_N256-16384_eps1e-4",
@@ -625,7 +627,7 @@ def ensemble_bench(args):
     precs = ("mixed", "fp64") if args.prec == "both" else (args.prec,)
     prec_of = {"mixed": nb.NB_MIXED, "fp64": nb.NB_FP64, "ex": nb.NB_EX}
     def shapes_for(prec_name):
-        spec = args.ens_shapes or ("4x128" if prec_name == "mixed" else "8x128x256")
+        spec = args.ens_shapes or "0x128x0"      # 0: the library's default for the precision
         out = [tuple(int(q) for q in sh.split("x")) for sh in spec.split(",")]
         return [sh if len(sh) == 3 else (sh[0], sh[1], 0) for sh in out]
     everyone = list(range(sizes.size))

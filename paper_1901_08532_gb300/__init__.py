@@ -86,6 +86,7 @@ _lib.nb_evaluate_fp64_static.restype = C.c_int
 _lib.nb_ensemble_init.argtypes = [C.POINTER(C.c_void_p), C.c_int32, _i64, _d, _d, _d, C.c_double,
                                   C.POINTER(Config)]
 _lib.nb_ensemble_set_shape.argtypes = [_vp, C.c_int32, C.c_int32, C.c_int32]
+_lib.nb_ensemble_get_shape.argtypes = [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
 _lib.nb_ensemble_run.argtypes = [_vp, C.c_double, C.c_int]
 _lib.nb_ensemble_get_state.argtypes = [_vp] + [_d] * 8
 _lib.nb_ensemble_stats.argtypes = [_vp, _i64, _d, _i64]
@@ -93,8 +94,8 @@ _lib.nb_ensemble_last_error.argtypes = [_vp]
 _lib.nb_ensemble_last_error.restype = C.c_char_p
 _lib.nb_ensemble_free.argtypes = [_vp]
 _lib.nb_ensemble_free.restype = None
-for _f in ("nb_ensemble_init", "nb_ensemble_set_shape", "nb_ensemble_run", "nb_ensemble_get_state",
-           "nb_ensemble_stats"):
+for _f in ("nb_ensemble_init", "nb_ensemble_set_shape", "nb_ensemble_get_shape", "nb_ensemble_run",
+           "nb_ensemble_get_state", "nb_ensemble_stats"):
     getattr(_lib, _f).restype = C.c_int
 _lib.nb_pairs_workspace_bytes.argtypes = [C.c_int64]
 _lib.nb_pairs_workspace_bytes.restype = C.c_size_t
@@ -117,7 +118,8 @@ EXPORTED = ("nb_config_default", "nb_init", "nb_predict", "nb_get_predicted", "n
             "nb_run_until", "nb_run_diag", "nb_energy", "nb_angmom", "nb_get_state", "nb_set_state",
             "nb_get_active", "nb_set_tiles", "nb_resolve_tiles", "nb_counters", "nb_inject_fault",
             "nb_evaluate_fp64_static", "nb_last_error", "nb_free", "nb_ensemble_init",
-            "nb_ensemble_set_shape", "nb_ensemble_run", "nb_ensemble_get_state", "nb_ensemble_stats",
+            "nb_ensemble_set_shape", "nb_ensemble_get_shape", "nb_ensemble_run", "nb_ensemble_get_state",
+            "nb_ensemble_stats",
             "nb_ensemble_last_error", "nb_ensemble_free", "nb_pairs_workspace_bytes", "nb_pairs_fp64",
             "nb_pairs_fp64_adjoint")
 
@@ -376,12 +378,15 @@ class Ensemble:
 
     def set_shape(self, ctas_per_system=None, threads=128, jtile=None):
         """Blocks per system, threads per block, j-tile length (None: the
-        library's default for the precision)."""
-        if ctas_per_system is None:
-            ctas_per_system = 4 if self.precision == NB_MIXED else 8
-        if jtile is None:
-            jtile = 1024 if self.precision == NB_MIXED else 256
-        self._check(_lib.nb_ensemble_set_shape(self._e, int(ctas_per_system), int(threads), int(jtile)))
+        library's default for the precision and device)."""
+        self._check(_lib.nb_ensemble_set_shape(self._e, int(ctas_per_system or 0), int(threads or 0),
+                                               int(jtile or 0)))
+
+    def shape(self):
+        """(blocks per system, threads per block, j-tile) in use."""
+        g, t, j = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(_lib.nb_ensemble_get_shape(self._e, C.byref(g), C.byref(t), C.byref(j)))
+        return g.value, t.value, j.value
 
     def run(self, t_end, use_graph=True):
         self._check(_lib.nb_ensemble_run(self._e, float(t_end), 1 if use_graph else 0))

@@ -107,7 +107,8 @@ ENSEMBLE_SPACE = {"ctas_per_system": (2, 4, 8, 16), "threads": (64, 128, 256), "
 
 def ensemble_candidates(precision: int):
     """Ensemble launch shapes worth timing (blocks per system, threads per
-    block, j-tile), the library's default for the precision first."""
+    block, j-tile): a portable starting shape for the precision first (mixed
+    4 x 128, j-tile 1024; otherwise 8 x 128, j-tile 256), then the space."""
     default = (4, 128, 1024) if precision == 1 else (8, 128, 256)
     yield default
     for g in ENSEMBLE_SPACE["ctas_per_system"]:

@@ -1131,6 +1131,27 @@ cudaError_t max_clusters(nb_ensemble *e, int *out)
     return cudaOccupancyMaxActiveClusters(out, ensemble_kernel<PR>, &cfg);
 }
 
+// Default blocks per system: mixed ensembles 4 (their steps are latency-
+// bound); FP64 and EX ensembles, whose steps carry most of the arithmetic,
+// 16 where the device co-schedules clusters of 16 blocks, else 8.
+int default_ctas(nb_ensemble *e)
+{
+    if (e->cfg.precision == NB_MIXED)
+        return 4;
+    const int keep = e->G;
+    e->G = 16;
+    int maxc = 0;
+    const cudaError_t err = ens_kind(e) == 2 ? max_clusters<2>(e, &maxc) : max_clusters<0>(e, &maxc);
+    e->G = keep;
+    if (err != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 8;
+    }
+    return maxc >= 1 ? 16 : 8;
+}
+
+int default_jtile(const nb_ensemble *e) { return e->cfg.precision == NB_MIXED ? 1024 : 256; }
+
 EnsArgs make_args(nb_ensemble *e, int mode, double t_end)
 {
     EnsArgs a;
@@ -1291,9 +1312,9 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
     e->nc = n_systems;
     e->P = padded;
     // defaults from shape sweeps on GB300: mixed 4 x 128 threads, j-tile
-    // 1024; FP64 and EX (evaluation-heavy steps) 8 x 128, j-tile 256 (the
-    // largest portable cluster; 16 blocks, non-portable, gain a further ~10 %)
-    e->jtile = cf.precision == NB_MIXED ? 1024 : 256;
+    // 1024; FP64 and EX 16 (or 8) x 128, j-tile 256 (set below, once the
+    // device is known)
+    e->jtile = default_jtile(e);
     e->G = cf.precision == NB_MIXED ? 4 : 8;
     auto bail = [&](nb_status s) {
         nb_set_thread_error(e->err.c_str());
@@ -1316,6 +1337,7 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
         EI(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
         e->own_stream = true;
     }
+    e->G = default_ctas(e);
     e->off.resize(n_systems);
     e->cnt.resize(n_systems);
     {
@@ -1413,13 +1435,17 @@ nb_status nb_ensemble_set_shape(nb_ensemble *e, int32_t ctas_per_system, int32_t
         return NB_EINVAL;
     if (e->dead)
         return NB_ECUDA;
-    if (ctas_per_system < 1 || ctas_per_system > kMaxCluster || threads < 64 || threads > kEnsThreads ||
+    if (threads == 0)
+        threads = 128;
+    if (jtile == 0)
+        jtile = default_jtile(e);
+    if (ctas_per_system < 0 || ctas_per_system > kMaxCluster || threads < 64 || threads > kEnsThreads ||
         threads % 32 || jtile < 4 || jtile > 1024 || jtile % 4)
-        return efail(e, NB_EINVAL, "ctas_per_system in [1, 16], threads a multiple of 32 in [64, 256], "
-                                   "jtile a multiple of 4 in [4, 1024]");
-    e->G = ctas_per_system;
+        return efail(e, NB_EINVAL, "ctas_per_system in [0, 16], threads 0 or a multiple of 32 in [64, 256], "
+                                   "jtile 0 or a multiple of 4 in [4, 1024]");
     e->threads = threads;
     e->jtile = jtile;
+    e->G = ctas_per_system == 0 ? default_ctas(e) : ctas_per_system;
     if (e->exec) {
         cudaGraphExecDestroy(e->exec);
         e->exec = nullptr;
@@ -1509,6 +1535,19 @@ nb_status nb_ensemble_get_state(nb_ensemble *e, double *x, double *v, double *a,
             if (dt)
                 dt[dst] = hdt[i];
         }
+    return NB_OK;
+}
+
+nb_status nb_ensemble_get_shape(nb_ensemble *e, int32_t *ctas_per_system, int32_t *threads, int32_t *jtile)
+{
+    if (!e)
+        return NB_EINVAL;
+    if (ctas_per_system)
+        *ctas_per_system = e->G;
+    if (threads)
+        *threads = e->threads;
+    if (jtile)
+        *jtile = e->jtile;
     return NB_OK;
 }
 

@@ -35,3 +35,41 @@ def nb_gpu():
         pytest.skip("no CUDA device")
     import paper_1901_08532_gb300 as nb
     return nb
+
+
+_GOLDEN = __import__("pathlib").Path(__file__).resolve().parent / "golden"
+_EXPR = __import__("re").compile(r"^[0-9eE+\-*/(). ]*(sqrt[0-9eE+\-*/(). ]*)*$")
+
+
+def _value(tok):
+    """One number of a fixture: integer, decimal, fraction p/q or a closed
+    form in sqrt(), evaluated in FP64 (true division of exact integers is
+    correctly rounded)."""
+    import math
+    assert _EXPR.match(tok), tok
+    return float(eval(tok, {"__builtins__": {}}, {"sqrt": math.sqrt}))
+
+
+def load_golden(name):
+    """The cases of a text fixture under tests/golden: a list of dicts with
+    "name", scalars (one value), vectors (three values) and, for "body"
+    lines, an [n, 7] array (m, x, y, z, vx, vy, vz)."""
+    cases = []
+    for raw in (_GOLDEN / name).read_text().splitlines():
+        line = raw.split("#", 1)[0].strip()
+        if not line:
+            continue
+        key, rest = line.split(None, 1)
+        if key == "case":
+            cases.append({"name": rest.strip(), "body": []})
+            continue
+        case = cases[-1]
+        if key == "body":
+            case["body"].append([_value(t) for t in rest.split()])
+        elif key in ("epot", "Lnorm", "ekin", "m_j", "eps"):
+            case[key] = _value(rest.strip())
+        else:
+            case[key] = np.array([_value(t) for t in rest.split()])
+    for case in cases:
+        case["body"] = np.array(case["body"]) if case["body"] else None
+    return cases

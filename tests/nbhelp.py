@@ -1,4 +1,7 @@
-"""Shared helpers for the parity tests (error metrics, GPU import)."""
+"""Shared helpers for the parity tests (error metrics, GPU import, the
+worked-example fixtures under tests/golden)."""
+import pathlib
+
 import numpy as np
 import pytest
 
@@ -37,17 +40,37 @@ def nb_gpu():
     return nb
 
 
-_GOLDEN = __import__("pathlib").Path(__file__).resolve().parent / "golden"
-_EXPR = __import__("re").compile(r"^[0-9eE+\-*/(). ]*(sqrt[0-9eE+\-*/(). ]*)*$")
+_GOLDEN = pathlib.Path(__file__).resolve().parent / "golden"
 
 
 def _value(tok):
     """One number of a fixture: integer, decimal, fraction p/q or a closed
-    form in sqrt(), evaluated in FP64 (true division of exact integers is
-    correctly rounded)."""
+    form built from numbers, + - * / and sqrt(), evaluated in FP64 (true
+    division of exact integers is correctly rounded).  Anything else in the
+    expression is rejected."""
+    import ast
     import math
-    assert _EXPR.match(tok), tok
-    return float(eval(tok, {"__builtins__": {}}, {"sqrt": math.sqrt}))
+    import operator
+
+    ops = {ast.Add: operator.add, ast.Sub: operator.sub, ast.Mult: operator.mul,
+           ast.Div: operator.truediv}
+
+    def ev(node):
+        if isinstance(node, ast.Expression):
+            return ev(node.body)
+        if isinstance(node, ast.Constant) and type(node.value) in (int, float):
+            return node.value
+        if isinstance(node, ast.UnaryOp) and isinstance(node.op, (ast.USub, ast.UAdd)):
+            x = ev(node.operand)
+            return -x if isinstance(node.op, ast.USub) else x
+        if isinstance(node, ast.BinOp) and type(node.op) in ops:
+            return ops[type(node.op)](ev(node.left), ev(node.right))
+        if (isinstance(node, ast.Call) and isinstance(node.func, ast.Name)
+                and node.func.id == "sqrt" and len(node.args) == 1 and not node.keywords):
+            return math.sqrt(ev(node.args[0]))
+        raise ValueError(f"unsupported fixture value {tok!r}")
+
+    return float(ev(ast.parse(tok, mode="eval")))
 
 
 def load_golden(name):

@@ -239,13 +239,18 @@ void orc_interpolate(double h, const double a0[3], const double j0[3],
 
 /* --------------------------------------------------------------- time step */
 
-/* Generalised Aarseth criterion (section 3 item 3) in the 6th-order form. */
+/* Generalised Aarseth criterion (section 3 item 3) in the 6th-order form.
+ * A particle under no force at all (every derivative exactly zero, as for a
+ * lone particle) gives A1 = A4 = 0: the ratio then carries no information
+ * and sets no bound (+infinity, which the quantiser maps to dt_max). */
 double orc_dt_crit(double eta, const double a[3], const double j[3],
                    const double s[3], const double c[3], const double d[3],
                    const double e[3])
 {
     double A1 = sqrt(norm3(a) * norm3(s)) + norm3(j);
     double A4 = sqrt(norm3(c) * norm3(e)) + norm3(d);
+    if (A1 == 0.0 && A4 == 0.0)
+        return INFINITY;
     return eta * cbrt(A1 / A4);
 }
 
@@ -253,9 +258,10 @@ double orc_dt_initial(double eta_s, const double a[3], const double j[3],
                       const double s[3])
 {
     double na = norm3(a), nj = norm3(j), ns = norm3(s);
-    double t1 = na / nj;
-    double t2 = sqrt(na / ns);
-    return eta_s * (t1 < t2 ? t1 : t2);
+    /* a ratio 0/0 sets no bound; fmin takes the bound that exists */
+    double t1 = (na == 0.0 && nj == 0.0) ? INFINITY : na / nj;
+    double t2 = (na == 0.0 && ns == 0.0) ? INFINITY : sqrt(na / ns);
+    return eta_s * fmin(t1, t2);
 }
 
 double orc_dt_quantise(double dt_crit, double dt_old, double t1, double dt_min,

@@ -61,13 +61,14 @@ void orc_interpolate(double h, const double a0[3], const double j0[3],
                      const double s1[3], double c1[3], double d1[3], double e1[3]);
 
 /* Generalised Aarseth criterion for a 6th-order scheme (section 3 item 3):
- * eta * (A1 / A4)^(1/3), A_k = sqrt(|a^(k-1)| |a^(k+1)|) + |a^(k)|. */
+ * eta * (A1 / A4)^(1/3), A_k = sqrt(|a^(k-1)| |a^(k+1)|) + |a^(k)|;
+ * +infinity (no bound) when A1 = A4 = 0, a particle under no force. */
 double orc_dt_crit(double eta, const double a[3], const double j[3],
                    const double s[3], const double c[3], const double d[3],
                    const double e[3]);
 
 /* Starting step before any interpolation exists:
- * eta_s * min(|a|/|j|, sqrt(|a|/|s|)). */
+ * eta_s * min(|a|/|j|, sqrt(|a|/|s|)), a ratio 0/0 counting as no bound. */
 double orc_dt_initial(double eta_s, const double a[3], const double j[3],
                       const double s[3]);
 

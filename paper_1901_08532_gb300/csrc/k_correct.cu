@@ -14,6 +14,7 @@
 
 namespace {
 
+using nbk::initial_dt;
 using nbk::quantise;
 
 struct CorrectArgs {
@@ -77,9 +78,7 @@ __global__ void init_state_kernel(double *st, double *dt, const double *anew, in
     if (dt_shared > 0.0) {
         d0 = dt_shared;
     } else {
-        na = sqrt(na);
-        const double c1 = na / sqrt(nj), c2 = sqrt(na / sqrt(ns));
-        d0 = quantise(eta_s * fmin(c1, c2), -1.0, 0.0, dt_min, dt_max, &hit);
+        d0 = quantise(initial_dt(sqrt(na), nj, ns, eta_s), -1.0, 0.0, dt_min, dt_max, &hit);
     }
     dt[i] = d0;
     if (hit)

@@ -530,7 +530,8 @@ __device__ void correct_one_mixed(const EnsArgs &a, int i, double tn, const doub
                          norm3f(jn[0], jn[1], jn[2]);
         const float A4 = sqrtf(norm3f(cn[0], cn[1], cn[2])) * sqrtf(norm3f(en[0], en[1], en[2])) +
                          norm3f(dn[0], dn[1], dn[2]);
-        const float crit = static_cast<float>(a.eta) * cbrtf(A1 / A4);
+        // A1 = A4 = 0: no force, no bound (dt_max), as in aarseth_dt()
+        const float crit = (A1 == 0.0f && A4 == 0.0f) ? INFINITY : static_cast<float>(a.eta) * cbrtf(A1 / A4);
         a.dt[i] = quantise(static_cast<double>(crit), a.dt[i], tn, a.dt_min, a.dt_max, &hit);
     }
     if (hit)
@@ -867,9 +868,7 @@ __device__ void init_share(const EnsArgs &a, int off, int s0, int s1, int pass)
         if (a.dt_shared > 0.0) {
             a.dt[i] = a.dt_shared;
         } else {
-            na = sqrt(na);
-            a.dt[i] = quantise(a.eta_s * fmin(na / sqrt(nj), sqrt(na / sqrt(ns))), -1.0, 0.0, a.dt_min,
-                               a.dt_max, &hit);
+            a.dt[i] = quantise(initial_dt(sqrt(na), nj, ns, a.eta_s), -1.0, 0.0, a.dt_min, a.dt_max, &hit);
         }
         if (hit)
             atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->floor_hits), 1ull);

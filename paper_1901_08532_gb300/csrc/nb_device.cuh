@@ -198,11 +198,24 @@ __device__ __forceinline__ Corrected hermite_correct(double h, double ih, double
 // Generalised Aarseth criterion in the 6th-order form from the squared
 // norms n2 = |a|^2, |j|^2, |s|^2, |c|^2, |d|^2, |e|^2:
 // eta (A1 / A4)^(1/3), A1 = sqrt(|a| |s|) + |j|, A4 = sqrt(|c| |e|) + |d|.
+// A1 = A4 = 0 (a particle under no force, e.g. a lone one) sets no bound:
+// +infinity, which quantise() maps to dt_max.
 __device__ __forceinline__ double aarseth_dt(const double (&n2)[6], double eta)
 {
     const double A1 = sqrt(sqrt(n2[0]) * sqrt(n2[2])) + sqrt(n2[1]);
     const double A4 = sqrt(sqrt(n2[3]) * sqrt(n2[5])) + sqrt(n2[4]);
+    if (A1 == 0.0 && A4 == 0.0)
+        return INFINITY;
     return eta * cbrt(A1 / A4);
+}
+
+// Starting step eta_s min(|a|/|j|, sqrt(|a|/|s|)) from |a| and the squared
+// norms of j and s; a ratio 0/0 sets no bound (+infinity).
+__device__ __forceinline__ double initial_dt(double na, double nj2, double ns2, double eta_s)
+{
+    const double c1 = (na == 0.0 && nj2 == 0.0) ? INFINITY : na / sqrt(nj2);
+    const double c2 = (na == 0.0 && ns2 == 0.0) ? INFINITY : sqrt(na / sqrt(ns2));
+    return eta_s * fmin(c1, c2);
 }
 
 }  // namespace nbk

@@ -128,3 +128,24 @@ def test_ex_ensemble_launch_shapes_agree_and_track_fp64():
             assert rel_err(st[f], out[0][f]).max() < 1e-12, f
             assert rel_err(st[f], st64[f]).max() < 1e-11, f
         np.testing.assert_array_equal(st["t"], st64["t"])
+
+
+@pytest.mark.parametrize("prec", [0, 1, 3])
+def test_lone_particle_system_coasts_at_the_largest_step(prec):
+    """A one-particle system feels no force: its step criterion is 0/0 and
+    sets no bound, so it coasts in a straight line at dt_max (exactly, with
+    dyadic inputs) beside systems that do interact."""
+    nb = nb_gpu()
+    ms, xs, vs = _systems([2, 33], 90)
+    m1, x1, v1 = np.ones(1), np.array([[0.25, -0.5, 1.0]]), np.array([[0.5, 0.125, -1.0]])
+    sizes = [1, 2, 33]
+    ens = nb.Ensemble(sizes, *_concat([m1] + ms, [x1] + xs, [v1] + vs), 1e-4, precision=prec)
+    ens.run(0.25)
+    st = ens.state()
+    steps, _, _ = ens.stats()
+    ens.close()
+    assert steps[0] == 2
+    np.testing.assert_array_equal(st["x"][0], x1[0] + 0.25 * v1[0])
+    np.testing.assert_array_equal(st["v"][0], v1[0])
+    assert st["dt"][0] == 0.125 and st["t"][0] == 0.25
+    assert np.isfinite(st["x"]).all() and (st["t"] == 0.25).all()

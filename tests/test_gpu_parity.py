@@ -274,6 +274,27 @@ def test_empty_active_set_and_argument_errors():
     assert e.value.status == nb.NB_ENONFINITE
 
 
+@pytest.mark.parametrize("device_steps", [True, False])
+@pytest.mark.parametrize("prec", [0, 1, 3])
+def test_lone_particle_coasts_at_the_largest_step(prec, device_steps):
+    """N = 1, the method's degenerate system: no force, so the step
+    criterion is 0/0, sets no bound, and the particle moves in a straight
+    line at dt_max, exactly as the oracle's lone particle does."""
+    nb = nb_gpu()
+    x0, v0 = np.array([[0.25, -0.5, 1.0]]), np.array([[0.5, 0.125, -1.0]])
+    g = nb.NBody(np.ones(1), x0, v0, 1e-4, precision=prec, device_steps=device_steps)
+    steps, _ = g.run_until(0.5)
+    st = g.state()
+    g.close()
+    ref = O.System(np.ones(1), x0, v0, 1e-4)
+    ref_steps, _ = ref.run_until(0.5)
+    sr = ref.state()
+    assert steps == ref_steps == 4
+    for f in ("x", "v", "t", "dt"):
+        np.testing.assert_array_equal(st[f], sr[f], err_msg=f)
+    np.testing.assert_array_equal(st["x"], x0 + 0.5 * v0)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_full_size_sampled_parity(prec):
     """N = 2^20 Plummer with Salpeter masses, eps = 1e-4, active fraction

@@ -224,6 +224,32 @@ def test_initial_step():
     assert O.dt_initial(0.01, a, j, s) == pytest.approx(0.01 * 0.25, rel=1e-15)
 
 
+def test_no_force_sets_no_bound():
+    """A particle under no force (every derivative exactly zero) gives the
+    ratios 0/0: no bound, so the quantised step is dt_max and no floor hit.
+    A zero acceleration beside a non-zero jerk still gives the bound 0."""
+    z = np.zeros(3)
+    assert O.dt_crit(0.4, z, z, z, z, z, z) == math.inf
+    assert O.dt_initial(0.01, z, z, z) == math.inf
+    assert O.dt_quantise(math.inf, -1, 0.0) == (0.125, False)
+    assert O.dt_initial(0.01, z, np.array([0, 1.0, 0]), z) == 0.0
+    # one ratio 0/0, the other a real bound: the real bound is taken
+    a, s = np.array([4.0, 0, 0]), np.array([0, 0, 1.0])
+    assert O.dt_initial(0.01, a, z, s) == pytest.approx(0.02, rel=1e-15)
+
+
+def test_lone_particle_coasts_at_the_largest_step():
+    """N = 1: no force, so straight-line motion at dt_max, exactly."""
+    x0, v0 = np.array([[0.25, -0.5, 1.0]]), np.array([[0.5, 0.125, -1.0]])
+    sys1 = O.System(np.ones(1), x0, v0, 1e-4)
+    steps, _ = sys1.run_until(0.5)
+    st = sys1.state()
+    assert steps == 4 and sys1.floor_hits == 0
+    np.testing.assert_array_equal(st["dt"], [0.125])
+    np.testing.assert_array_equal(st["x"], x0 + 0.5 * v0)
+    np.testing.assert_array_equal(st["v"], v0)
+
+
 @pytest.mark.parametrize("crit,old,t1,want,hit", [
     (0.3, -1, 0.0, 0.125, False),          # clamp to dt_max
     (float("inf"), -1, 0.0, 0.125, False),  # unbounded criterion -> dt_max

@@ -55,7 +55,7 @@ PEAK_FP32_OPS = SM_COUNT * 128 * SM_MAX_MHZ * 1e6                 # 40.3e12 / s
 # DRAM traffic of one mixed evaluation launch (the bench's own launch, one
 # ncu pass); valid only for the kernel source it was measured on (the sha256
 # prefix of csrc/k_eval.cu and csrc/nb_device.cuh).
-TRAFFIC = {"kernel_sha": "f48d47d3a8d9b0db", "bytes_per_launch": 119.15e6 + 69.61e6,
+TRAFFIC = {"kernel_sha": "9c93c07bc089f7e9", "bytes_per_launch": 126.36e6 + 70.11e6,
            "source": "profiles/eval_mixed_dram_plummer_N1048576_all_active.md"}
 WORKLOAD = "plummer_salpeter_N1048576_eps1e-4_shared_step_all_active"
 METRIC = "acc+jerk+snap interactions/s at N=2^20, mixed vs FP64 at rel err <= 1e-6"

@@ -19,8 +19,8 @@ The CPU leg runs the FP64 CPU oracle on the host cores: one core on 48
 sampled i-particles, then one instance per core on disjoint rows of a seeded
 4096-particle subset (all against the 2^20 j); the oracle's sums for that
 subset check both GPU paths (err_vs_oracle).  --impl reference times the
-oracle (the reference arm) on the host cores for the same workload, one
-bounded i-sample per step.
+oracle (the reference arm) on the host cores for the same workload: one
+instance per core, 16 sampled i-particles each per step.
 """
 from __future__ import annotations
 
@@ -181,29 +181,40 @@ def _cpu_model():
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands (single-threaded C),
+    one independent instance per usable host core on disjoint i-rows of the
+    seeded 4096-particle subset, each against all n j.  A step is one round of
+    `rows` i-particles per instance; its time is the slowest instance's (they
+    run concurrently)."""
     rank = _env_int("RANK", 0)
     if rank != 0:
         return 0
-    n = args.n
-    rows = 16
-    import nb_inputs as ni  # noqa: F401
-    for _ in range(args.warmup):
-        _oracle_worker((0, 2, n))
-    times = []
-    for s in range(args.steps):
-        times.append(_oracle_worker((s * rows % 4096, s * rows % 4096 + rows, n)))
-    value = rows * n * len(times) / sum(times)
+    import multiprocessing as mp
+    n, rows, sample = args.n, 16, 4096
+    k = max(1, min(len(os.sched_getaffinity(0)), sample // rows))
+
+    def jobs(s):
+        return [(((s * k + r) * rows) % sample, ((s * k + r) * rows) % sample + rows, n)
+                for r in range(k)]
+
+    with mp.get_context("spawn").Pool(k) as pool:
+        for w in range(args.warmup):
+            pool.map(_oracle_worker, jobs(w))
+        times = [max(pool.map(_oracle_worker, jobs(args.warmup + s))) for s in range(args.steps)]
+    value = k * rows * n * len(times) / sum(times)
+    sample_txt = (f"{k} oracle instances x {rows} i-particles of a seeded {sample}-i subset "
+                  f"x all {n} j per step")
     line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "interactions/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "eps": EPS, "seed": SEED, "imf": "salpeter",
-                       "arm": "FP64 CPU oracle (single-threaded C), the reference arm of a paper "
-                              "without code",
-                       "step": f"oracle evaluation of {rows} sampled i x all {n} j"},
-            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{rows} i-particles of a seeded 4096-i subset x all {n} j per step"},
+                       "arm": "FP64 CPU oracle (single-threaded C, one instance per host core), "
+                              "the reference arm of a paper without code",
+                       "step": f"oracle evaluation of {k * rows} sampled i x all {n} j"},
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": k, "kind": "oracle",
+                             "sample": sample_txt, "host_cpu": _cpu_model()},
             "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

@@ -304,6 +304,7 @@ nb_status nb_ensemble_stats(nb_ensemble *e, int64_t *steps, double *interactions
  * on this thread). */
 const char *nb_ensemble_last_error(const nb_ensemble *e);
 
+/* Release the ensemble and all of its device memory.  NULL is allowed. */
 void nb_ensemble_free(nb_ensemble *e);
 
 /* ---------------------------------------------------------------------------

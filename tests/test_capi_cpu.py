@@ -61,3 +61,22 @@ def test_init_rejects_bad_arguments_without_a_gpu():
     assert lib.nb_init(C.byref(ctx), 4, p(m), p(bad), p(x), 1e-3, None) == nb.NB_ENONFINITE
     assert ctx.value is None
     lib.nb_free(None)
+
+
+def test_every_declaration_is_documented():
+    """Each entry point in include/nb.h is preceded by its own comment (the
+    operation, argument meaning and layout, ownership, errors)."""
+    lines = open(os.path.join(ROOT, "include", "nb.h")).read().splitlines()
+    decl = re.compile(r"^(nb_status|void|const char \*)\s*\**\s*(nb_[a-z_0-9]+)\s*\(")
+    found, bad = 0, []
+    for k, line in enumerate(lines):
+        m = decl.match(line)
+        if not m:
+            continue
+        found += 1
+        j = k - 1
+        while j >= 0 and not lines[j].strip():
+            j -= 1
+        if not lines[j].rstrip().endswith("*/"):
+            bad.append(m.group(2))
+    assert found >= 30 and not bad, bad

@@ -59,6 +59,24 @@ def test_pair_self_term_is_zero_and_antisymmetric():
 
 # ------------------------------------------------------------ evaluation sum
 
+@pytest.mark.parametrize("lam,tau", [(2.0, 4.0), (0.25, 0.5), (8.0, 0.125)])
+def test_units_scaling_law_is_exact(lam, tau):
+    """Change of units x -> lam x, t -> tau t (G = 1 kept, so m -> lam^3 /
+    tau^2 m, and eps -> lam eps): acc, jerk and snap scale by lam / tau^2,
+    lam / tau^3 and lam / tau^4.  With powers of two every rounding scales
+    too, so the identity holds bit for bit; a wrong power of q or a
+    misplaced factor in any term breaks it."""
+    n, eps = 64, 1e-3
+    m, x, v = ni.plummer(n, 41, imf="salpeter")
+    a = ni.random_state(n, 42, scale=2.0)
+    act = ni.active_subset(n, 17, 43)
+    ref = O.evaluate(m, x, v, a, eps, act)
+    got = O.evaluate(m * lam ** 3 / tau ** 2, x * lam, v * lam / tau, a * lam / tau ** 2,
+                     eps * lam, act)
+    for k, (g, r) in enumerate(zip(got, ref)):
+        np.testing.assert_array_equal(g, r * lam / tau ** (2 + k))
+
+
 def test_newton_third_law_for_acc_jerk_snap():
     m, x, v = ni.plummer(256, 5, imf="salpeter")
     a = ni.random_state(256, 6)

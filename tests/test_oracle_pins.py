@@ -103,6 +103,44 @@ def test_evaluate_equals_sum_of_pairs_and_skips_self():
         np.testing.assert_allclose(snp[k], tot[2], rtol=1e-13)
 
 
+def test_compensated_sum_survives_cancellation():
+    """Antipodal pairs around particle 0, in shuffled order, cancel exactly;
+    one faint distant particle leaves a result far below the terms' size.
+    The oracle's compensated sums must equal the correctly rounded sum of
+    its own pair terms (math.fsum) within the error bound of compensated
+    summation, 2u|S| + n u^2 sum|x_i| (Higham, Accuracy and Stability of
+    Numerical Algorithms, section 4.3), which plain left-to-right summation
+    exceeds by orders of magnitude."""
+    rng = np.random.default_rng(51)
+    k = 100
+    d = rng.standard_normal((k, 3)) * rng.uniform(0.5, 2.0, (k, 1))
+    xs = np.concatenate([d, -d, [[40.0, 30.0, 0.0]]])
+    vs = np.concatenate([rng.standard_normal((k, 3)), np.zeros((k + 1, 3))])
+    vs[k:2 * k] = -vs[:k]                                 # antipodal velocities too
+    vs[-1] = [0.1, -0.2, 0.3]                             # the faint particle moves
+    ms = np.concatenate([rng.uniform(0.5, 1.5, k), np.zeros(k + 1)])
+    ms[k:2 * k] = ms[:k]
+    ms[-1] = 1e-6
+    order = rng.permutation(xs.shape[0])
+    x = np.concatenate([[[0.0, 0.0, 0.0]], xs[order]])
+    v = np.concatenate([[[0.0, 0.0, 0.0]], vs[order]])
+    m = np.concatenate([[1.0], ms[order]])
+    a = np.zeros_like(x)
+    got = O.evaluate(m, x, v, a, 1e-3, [0])
+    terms = [O.pair(x[0], v[0], a[0], x[j], v[j], a[j], m[j], 1e-3) for j in range(1, m.size)]
+    u, n = 2.0 ** -53, len(terms)
+    for q in range(3):
+        exact = np.array([math.fsum(t[q][c] for t in terms) for c in range(3)])
+        total = np.array([math.fsum(abs(t[q][c]) for t in terms) for c in range(3)])
+        naive = np.zeros(3)
+        for t in terms:
+            naive += t[q]
+        bound = 2 * u * np.abs(exact) + n * u * u * total
+        assert np.abs(exact).max() > 0
+        assert np.all(np.abs(got[q][0] - exact) <= bound), q
+        assert np.abs(naive - exact).max() > 100 * bound.max(), q
+
+
 def test_jerk_and_snap_are_time_derivatives_of_acc():
     """Along x_k(tau) = x_k + v_k tau + a_k tau^2 / 2 for every particle,
     jerk_i = d acc_i / d tau and snap_i = d^2 acc_i / d tau^2 at tau = 0

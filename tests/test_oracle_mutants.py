@@ -22,7 +22,13 @@ MUTANTS = {
     "aarseth_swapped": ("sqrt(norm3(c) * norm3(e)) + norm3(d)", "sqrt(norm3(c) * norm3(d)) + norm3(e)"),
     "kinetic_half": ("0.5 * m[i] * dot3", "m[i] * dot3"),
     "quantise_off_by_one": ("p = ldexp(1.0, ex - 1);", "p = ldexp(1.0, ex);"),
+    "compensation_dropped": ("return s->sum + s->comp; }", "return s->sum; }"),
+    "potential_unsoftened": ("m[j] / sqrt(dot3(r, r) + eps * eps));", "m[j] / sqrt(dot3(r, r)));"),
+    "softening_not_squared": ("double R = dot3(r, r) + eps * eps;", "double R = dot3(r, r) + eps;"),
+    "angmom_z_sign": ("r[0] * u[1] - r[1] * u[0]};", "r[1] * u[0] - r[0] * u[1]};"),
+    "no_force_floor": ("    if (A1 == 0.0 && A4 == 0.0)\n        return INFINITY;\n", ""),
 }
+PIN_FILES = ("test_oracle_pins.py", "test_golden_cpu.py")
 
 
 @pytest.mark.slow
@@ -39,6 +45,7 @@ def test_pins_reject_mutant(name, tmp_path):
                     str(mut), "-o", str(so), "-lm"], check=True)
     env = dict(os.environ, NB_ORACLE_LIB=str(so))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        "--basetemp", str(tmp_path / "inner")]
+                       + [os.path.join(ROOT, "tests", f) for f in PIN_FILES],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"

@@ -128,7 +128,8 @@ void nb_config_default(nb_config *cfg);
  * evaluation pass with a_j = 0), then the snap (a second pass using those
  * accelerations), sets crackle to zero, t_i = 0 and the starting steps
  * (eta_s * min(|a|/|j|, sqrt(|a|/|s|)), rounded down to a power of two and
- * clamped to [dt_min, dt_max]).
+ * clamped to [dt_min, dt_max]; a ratio 0/0, as for a particle under no force,
+ * sets no bound, so such a particle starts at dt_max).
  * Errors: NB_EINVAL (n < 1, n > 2^31 - 1, eps <= 0, bad config), NB_ENONFINITE
  * (non-finite m, x or v, or m < 0), NB_ENOMEM, NB_ECUDA.  *out is NULL on error. */
 nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
@@ -165,7 +166,8 @@ nb_status nb_evaluate(nb_ctx *ctx, const int32_t *active, int64_t n_act,
 /* Corrector (section 3) for the particles of the last nb_evaluate, whose
  * prediction time must equal t: corrected x and v, the new a/jerk/snap,
  * crackle from quintic interpolation, t_i = t and a new step (generalised
- * Aarseth criterion, section 3 item 3; shared step when dt_shared > 0).
+ * Aarseth criterion, section 3 item 3, which sets no bound when every
+ * derivative is zero; shared step when dt_shared > 0).
  * Errors: NB_ESTATE (no matching evaluation), NB_ENONFINITE (a corrected
  * value is not finite). */
 nb_status nb_correct(nb_ctx *ctx, double t);

@@ -9,5 +9,9 @@ if ROOT not in sys.path:
 
 
 def pytest_configure(config):
+    # pytest creates --basetemp itself but not its parent directory
+    base = getattr(config.option, "basetemp", None)
+    if base:
+        os.makedirs(os.path.dirname(os.path.abspath(str(base))), exist_ok=True)
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: takes more than a few seconds on CPU")

@@ -41,9 +41,12 @@ N_BODY = 1 << 20
 EPS = 1e-4
 SEED = 3
 FLOPS_PER_INTERACTION = 78        # FMA = 2, rsqrt = 1 (counted against the pair formula)
+# SM count and maximum SM clock: GB300's, replaced by the device's own
+# (set_device_peaks) before any number is reported
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
-# plain-ALU peaks from unit counts and the maximum SM clock
+# plain-ALU peaks from unit counts (128 FP32 and 2 FP64 FMA lanes per SM) and
+# the maximum SM clock
 PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
 PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12     # 1.26
 # The extended-precision (double-word) kernel issues 496 FP32-pipe operations
@@ -52,11 +55,22 @@ PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12     # 1.26
 # per clock per SM.
 EX_OPS_PER_INTERACTION = 496
 PEAK_FP32_OPS = SM_COUNT * 128 * SM_MAX_MHZ * 1e6                 # 40.3e12 / s
+
+
+def set_device_peaks(torch, dev):
+    """Unit-count peaks of the current device: its SM count and maximum SM
+    clock (nvidia-smi clocks.max.sm)."""
+    global SM_COUNT, SM_MAX_MHZ, PEAK_FP32_TFLOPS, PEAK_FP64_TFLOPS, PEAK_FP32_OPS
+    SM_COUNT = torch.cuda.get_device_properties(dev).multi_processor_count
+    SM_MAX_MHZ = _max_sm_mhz(dev)
+    PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    PEAK_FP32_OPS = SM_COUNT * 128 * SM_MAX_MHZ * 1e6
 # DRAM traffic of one mixed evaluation launch (the bench's own launch, one
 # ncu pass); valid only for the kernel source it was measured on (the sha256
 # prefix of csrc/k_eval.cu and csrc/nb_device.cuh).
 TRAFFIC = {"kernel_sha": "9c93c07bc089f7e9", "bytes_per_launch": 126.36e6 + 70.11e6,
-           "source": "profiles/eval_mixed_dram_plummer_N1048576_all_active.md"}
+           "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass on this launch"}
 WORKLOAD = "plummer_salpeter_N1048576_eps1e-4_shared_step_all_active"
 METRIC = "acc+jerk+snap interactions/s at N=2^20, mixed vs FP64 at rel err <= 1e-6"
 
@@ -74,14 +88,21 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--shard", default="j", choices=["j", "replicas"],
+                   help="with N > 1 ranks: 'j' splits the j-particles of the one system over the "
+                        "ranks (the paper's multi-device evaluation: one all-reduce of the partial "
+                        "sums per step, strong scaling); 'replicas' runs an independent copy per "
+                        "rank (weak scaling)")
     p.add_argument("--n", type=int, default=N_BODY, help="particles (default 2^20)")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     p.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the other configurations' legs (ensemble, adjoint, N=65536 integration)")
     p.add_argument("--profile-eval", action="store_true",
                    help="only launch the evaluation kernel --reps times on --n particles with "
                         "--n-act active (a small case for ncu captures)")
     p.add_argument("--n-act", type=int, default=4096)
-    p.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "both", "ex", "sp"])
+    p.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "both", "ex", "sp", "mixed32"])
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--ensemble", action="store_true",
                    help="ensemble workload: 256 Plummer systems, N log-uniform in [256, 16384] "
@@ -112,10 +133,20 @@ def parse():
     p.add_argument("--ps-t-end", type=float, default=1.0)
     p.add_argument("--ps-dt", type=float, default=2.0 ** -3)
     p.add_argument("--ps-precs", default="fp64,mixed,ex,sp")
+    p.add_argument("--peaks", action="store_true",
+                   help="throughput probes of the CUDA-core pipes (FP32 FMA scalar and f32x2, FP64 "
+                        "FMA, special-function estimates, and packed FMAs mixed with estimates)")
     return p.parse_args()
 
 
 # ----------------------------------------------------------------- CPU leg
+
+def oracle_accel(ni, n):
+    """The acceleration inputs of the oracle comparison: a seeded synthetic
+    field (components uniform in [-2, 2]), so that the snap's a_j - a_i term
+    is exercised; the positions and velocities are the model's own."""
+    return ni.random_state(n, 5, scale=2.0)
+
 
 def _oracle_worker(args):
     """Oracle evaluation of i-rows [lo, hi) of the sample; returns seconds
@@ -128,7 +159,7 @@ def _oracle_worker(args):
     import nb_inputs as ni
     import oracle as O
     m, x, v = ni.plummer(n, SEED, imf="salpeter")
-    a = np.zeros_like(x)
+    a = oracle_accel(ni, n)
     act = ni.active_subset(n, sample, 31)[lo:hi]
     t0 = time.perf_counter()
     sums = O.evaluate(m, x, v, a, EPS, act)
@@ -320,6 +351,7 @@ def run_ours(args):
         cpu = cpu_baseline(n)          # before any GPU work (spawned pool)
 
     torch.cuda.set_device(local)
+    set_device_peaks(torch, local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -331,6 +363,11 @@ def run_ours(args):
     mixed = nb.NBody(m, x, v, EPS, precision=nb.NB_MIXED, dt_shared=2.0 ** -10, stream=stream)
     st = mixed.state()                      # starting a, jerk, snap from the mixed path
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    split = world > 1 and args.shard == "j"
+    lo, hi = 0, n
+    if split:
+        from paper_1901_08532_gb300.jsplit import reduce_partials, shard_bounds
+        lo, hi = shard_bounds(n, world, rank, 4)
 
     def barrier():
         torch.cuda.synchronize()
@@ -338,15 +375,24 @@ def run_ours(args):
             torch.distributed.barrier()
 
     def one_step(ctx, ev=None):
-        """Shared block step: predict all, evaluate all, correct all."""
+        """Shared block step: predict all, evaluate all (with N > 1 ranks in
+        j-split mode: this rank's j-range, then the all-reduce of the
+        partial sums), correct all."""
         flush.zero_()
         t = ctx_t[0] + 2.0 ** -10
         ctx.predict(t)
         if ev is not None:
             ev[0].record(stream)
-        ctx.evaluate(None, out=False)
-        if ev is not None:
-            ev[1].record(stream)
+        if split:
+            part = ctx.evaluate_partial(None, lo, hi)
+            if ev is not None:
+                ev[1].record(stream)
+            reduce_partials(part)
+            ctx.set_forces(None, part)
+        else:
+            ctx.evaluate(None, out=False)
+            if ev is not None:
+                ev[1].record(stream)
         ctx.correct(t)
         ctx_t[0] = t
 
@@ -356,28 +402,35 @@ def run_ours(args):
     launches0, inter0 = mixed.counters()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     with Clocks(local) as clk:
-        t0 = time.perf_counter()
+        e_start.record(stream)
         for k in range(args.steps):
             one_step(mixed, evs[k])
+        e_end.record(stream)
         barrier()
-        elapsed = time.perf_counter() - t0
+    elapsed = e_start.elapsed_time(e_end) / 1e3          # device time of the K steps
     launches1, inter1 = mixed.counters()
     eval_ms = [a.elapsed_time(b) for a, b in evs]
     elapsed, interactions = aggregate_ranks(elapsed, inter1 - inter0, "cuda")
     value = interactions / elapsed
     eval_s = sum(eval_ms) / len(eval_ms) / 1e3
-    achieved = FLOPS_PER_INTERACTION * float(n) * n / eval_s / 1e12
+    achieved = FLOPS_PER_INTERACTION * float(n) * (hi - lo) / eval_s / 1e12
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernel_sha"] == _kernel_sha() else None
     clocks = clk.summary()
+    peaks = measure_peaks(nb, torch)
+    peak_meas = peaks["fp32_tflops_at_max_clock"]
 
     extra = {}
     if not args.no_extra:
         extra = secondary(nb, np, torch, m, x, v, st, stream, n)
 
-    e2e = end_to_end(nb, np, torch, mixed, n, stream, max(1, min(args.steps, 3)))
+    e2e = end_to_end(nb, np, torch, mixed, n, stream, max(1, min(args.steps, 3)),
+                     (lo, hi, reduce_partials) if split else None)
     mixed.close()
+    if not args.no_configs and rank == 0 and world == 1:
+        extra["configs"] = config_legs(nb, np, torch, local)
     err_oracle = None
     if cpu is not None:
         err_oracle = error_vs_oracle(nb, np, torch, m, x, v, stream, *cpu.pop("_ref"))
@@ -386,21 +439,31 @@ def run_ours(args):
         "metric": METRIC,
         "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "strong" if split else "weak", "vs_baseline": None,
         "dtype": "f32", "precision": "mixed: FP32 pair arithmetic; FP64 positions (hi+lo FP32 "
                                      "pairs), FP64 prediction/correction, compensated accumulation",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "eps": EPS, "seed": SEED, "imf": "salpeter",
                    "step": "shared block step, all N active: predict + mixed evaluation + correct",
                    "l2": "flushed before every step (256 MB write inside the timed region)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "parallelism": (f"j-split x{world} (all-reduce of [9][N] FP64 partial sums per step)"
+                                   if split else f"replicas x{world}" if world > 1 else "single GPU"),
                    "flops_per_interaction": FLOPS_PER_INTERACTION},
         "roofline": {"bound": "alu", "kernel": "eval_mixed_kernel",
                      "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / PEAK_FP32_TFLOPS, "traffic": traffic,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit counts "
-                                    "and max clock)",
+                     "peak_source": f"{SM_COUNT} SMs x 128 FP32 lanes x 2 flops x {SM_MAX_MHZ:g} MHz "
+                                    "(unit counts and max clock)",
+                     "peak_measured": peak_meas, "frac_measured": achieved / peak_meas,
+                     "peak_measured_source": "nb_peak_probe: f32x2 FMA throughput "
+                                             f"{peaks['fp32_fma_per_clk_per_sm']:.1f}/clk/SM x 2 flops x "
+                                             f"{SM_COUNT} SMs x {SM_MAX_MHZ:g} MHz",
                      "eval_ms_mean": 1e3 * eval_s},
+        "peaks": {k: peaks[k] for k in ("fp32_fma_per_clk_per_sm", "fp64_fma_per_clk_per_sm",
+                                        "fp32_tflops_at_max_clock", "fp64_tflops_at_max_clock")} | {
+            "per_clk_per_sm": {k: round(v["ops_per_clk_per_sm"], 2) for k, v in peaks["kinds"].items()},
+            "est_per_clk_per_sm": {k: round(v["est_per_clk_per_sm"], 2) for k, v in peaks["kinds"].items()
+                                   if v["est_per_clk_per_sm"] > 0}},
         "e2e": e2e,
         "gpu_launches": int(launches1 - launches0),
         "clocks": clocks,
@@ -510,19 +573,26 @@ def secondary(nb, np, torch, m, x, v, st, stream, n):
 
 
 def error_vs_oracle(nb, np, torch, m, x, v, stream, act, sums, kap):
-    """Both GPU precisions on the oracle's sample (same inputs: a = 0 at
-    t = 0): per particle |d|_inf / |ref|_2, and |d|_inf / sum_j |T_ij| (the
-    error relative to the sum's condition number)."""
-    out = {"sample": int(len(act)), "inputs": "start positions and velocities, a = 0"}
+    """Both GPU precisions on the oracle's sample (same inputs: the start
+    positions and velocities, the seeded acceleration field of
+    oracle_accel, t = 0): per particle |d|_inf / |ref|_2 (max and the
+    fraction above 1e-6), and |d|_inf / sum_j |T_ij| (the error relative to
+    the sum's condition number)."""
+    import nb_inputs as ni
+    out = {"sample": int(len(act)),
+           "inputs": "start positions and velocities, seeded acceleration field (uniform [-2, 2])"}
+    a = oracle_accel(ni, m.size)
     for name, prec in (("mixed", nb.NB_MIXED), ("fp64", nb.NB_FP64)):
         ctx = nb.NBody(m, x, v, EPS, precision=prec, stream=stream, start_forces=False)
+        ctx.set_state({"a": a})
         ctx.predict(0.0)
         got = ctx.evaluate(act)
         ctx.close()
         rec = {}
         for q, g, r, k in zip(("acc", "jerk", "snap"), got, sums, kap):
             d = np.abs(g - r).max(axis=1)
-            rec[q] = {"max": float((d / np.linalg.norm(r, axis=1)).max()),
+            plain = d / np.linalg.norm(r, axis=1)
+            rec[q] = {"max": float(plain.max()), "frac_above_1e-06": float((plain > 1e-6).mean()),
                       "kappa_norm_max": float((d / k).max())}
         out[name] = rec
     out["mixed_within_1e-6_of_condition_number"] = all(
@@ -530,9 +600,10 @@ def error_vs_oracle(nb, np, torch, m, x, v, stream, act, sums, kap):
     return out
 
 
-def end_to_end(nb, np, torch, ctx, n, stream, steps):
+def end_to_end(nb, np, torch, ctx, n, stream, steps, split=None):
     """Same metric through the public API with pinned host buffers: upload
-    the full state, one shared block step, read back x and v."""
+    the full state, one shared block step, read back x and v.  split =
+    (lo, hi, reduce): the step evaluates j in [lo, hi) and all-reduces."""
     def pinned(shape):
         return torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
     st = ctx.state()
@@ -548,7 +619,11 @@ def end_to_end(nb, np, torch, ctx, n, stream, steps):
     def step():
         ctx._check(lib.nb_set_state(ctx._ctx, *[ptr(host[k]) for k in ("x", "v", "a", "j", "s", "c",
                                                                         "t", "dt")]))
-        ctx.step()
+        if split is None:
+            ctx.step()
+        else:
+            from paper_1901_08532_gb300.jsplit import jsplit_step
+            jsplit_step(ctx, split[0], split[1])
         ctx._check(lib.nb_get_state(ctx._ctx, ptr(outx), ptr(outv), None, None, None, None, None,
                                     None))
     step()
@@ -558,9 +633,13 @@ def end_to_end(nb, np, torch, ctx, n, stream, steps):
         step()
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
+    if split is not None:
+        el, _ = aggregate_ranks(el, 0.0, "cuda")     # the slowest rank's time
     return {"value": float(n) * n * steps / el, "unit": "interactions/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "api": "nb_set_state (pinned host) -> nb_step -> nb_get_state (pinned host)",
+            "api": ("nb_set_state (pinned host) -> nb_step -> nb_get_state (pinned host)" if split is None
+                    else "nb_set_state (pinned host) -> nb_schedule, nb_predict, nb_evaluate_partial, "
+                         "all-reduce, nb_set_forces, nb_correct -> nb_get_state (pinned host)"),
             "steps": steps}
 
 
@@ -636,7 +715,7 @@ def ensemble_bench(args):
     out = {"workload": f"ensemble_{args.ens_systems}_plummer_N256-16384_eps1e-4",
            "systems": int(sizes.size), "particles": int(sizes.sum())}
     precs = ("mixed", "fp64") if args.prec == "both" else (args.prec,)
-    prec_of = {"mixed": nb.NB_MIXED, "fp64": nb.NB_FP64, "ex": nb.NB_EX}
+    prec_of = {"mixed": nb.NB_MIXED, "fp64": nb.NB_FP64, "ex": nb.NB_EX, "mixed32": nb.NB_MIXED32}
     def shapes_for(prec_name):
         spec = args.ens_shapes or "0x128x0"      # 0: the library's default for the precision
         out = [tuple(int(q) for q in sh.split("x")) for sh in spec.split(",")]
@@ -650,7 +729,7 @@ def ensemble_bench(args):
             from paper_1901_08532_gb300.autotune import tune_ensemble
             order = np.argsort(sizes)
             pick = [int(order[q]) for q in np.linspace(0, sizes.size - 1, 32).astype(int)]
-            jts = (512, 1024) if prec_name == "mixed" else (256, 512)
+            jts = (512, 1024) if prec_name in ("mixed", "mixed32") else (256, 512)
             cands = [(g, thr, jt) for g in (2, 4, 8, 16) for thr in (64, 128) for jt in jts]
 
             def make(pick=pick, prec=prec):
@@ -696,22 +775,20 @@ def ensemble_bench(args):
     return 0
 
 
-def adjoint_bench(args):
-    """Config: Plummer N = 8192, eps = 1e-3, shared step 2^-10, 64 steps,
-    loss = sum m |x(T)|^2, gradients with respect to x0, v0, m through the
-    hand-written adjoint kernel with checkpoints every 8 steps."""
-    import numpy as np
-    import torch
-
+def adjoint_run(torch, n=8192, steps=64, checkpoint_every=8):
+    """Differentiable fixed-step trajectory: Plummer N = n (seed 5), eps =
+    1e-3, shared step 2^-10, `steps` steps, loss = sum m |x(T)|^2, gradients
+    with respect to x0, v0, m through the hand-written adjoints with
+    checkpoints every `checkpoint_every` steps.  Forward and forward+backward
+    timed with device synchronisation on both sides."""
     import nb_inputs as ni
     from paper_1901_08532_gb300 import adjoint as A
-    torch.cuda.set_device(0)
-    n = args.n if args.n != N_BODY else 8192
-    eps, h, steps = 1e-3, 2.0 ** -10, 64
+    eps, h = 1e-3, 2.0 ** -10
     m, x, v = ni.plummer(n, 5)
     mt, xt, vt = (torch.tensor(q, dtype=torch.float64, device="cuda") for q in (m, x, v))
     with torch.no_grad():
         A.trajectory(mt, xt, vt, eps, h, 2, 0)          # warm-up
+    A.loss_and_grads(mt, xt, vt, eps, h, 2, checkpoint_every=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     with torch.no_grad():
@@ -719,34 +796,36 @@ def adjoint_bench(args):
     torch.cuda.synchronize()
     fwd = time.perf_counter() - t0
     t0 = time.perf_counter()
-    L, gx, gv, gm = A.loss_and_grads(mt, xt, vt, eps, h, steps, checkpoint_every=8)
+    L, gx, gv, gm = A.loss_and_grads(mt, xt, vt, eps, h, steps, checkpoint_every=checkpoint_every)
     torch.cuda.synchronize()
     both = time.perf_counter() - t0
     inter_fwd = float(n) * n * (steps + 2)
-    print(json.dumps({"workload": f"adjoint_plummer_N{n}_eps1e-3_dt2^-10_64steps_ckpt8",
-                      "forward_s": fwd, "forward_interactions_per_s": inter_fwd / fwd,
-                      "forward_plus_backward_s": both, "backward_s": both - fwd,
-                      "backward_over_forward": (both - fwd) / fwd,
-                      "loss": float(L), "grad_norms": [float(g.norm()) for g in (gx, gv, gm)]}))
+    return {"workload": f"adjoint_plummer_N{n}_eps1e-3_dt2^-10_{steps}steps_ckpt{checkpoint_every}",
+            "forward_s": fwd, "forward_interactions_per_s": inter_fwd / fwd,
+            "forward_plus_backward_s": both, "backward_s": both - fwd,
+            "backward_over_forward": (both - fwd) / fwd,
+            "loss": float(L), "grad_norms": [float(g.norm()) for g in (gx, gv, gm)]}
+
+
+def adjoint_bench(args):
+    """Config: Plummer N = 8192, eps = 1e-3, shared step 2^-10, 64 steps,
+    loss = sum m |x(T)|^2, gradients with respect to x0, v0, m through the
+    hand-written adjoint kernels with checkpoints every 8 steps."""
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(adjoint_run(torch, args.n if args.n != N_BODY else 8192)))
     return 0
 
 
-def integrate_bench(args):
-    """Plummer N = 65536 (--prec fp64 by default in this mode's reference
-    config; ex and mixed also run): one full-N evaluation (2^32
-    interactions), then block-step integration to t = 1/16 through
-    nb_run_until (active sets from 1 to N particles)."""
-    import numpy as np
-    import torch
-
+def integrate_run(nb, np, torch, n, prec_name, t_end=1.0 / 16):
+    """Plummer N = n (equal masses, eps 1e-4, seed 2): one full-N evaluation
+    (n^2 interactions), then block-step integration to t_end through
+    nb_run_until (active sets from 1 to N particles), dt_max = 2^-4 so that
+    every particle synchronises at t_end."""
     import nb_inputs as ni
-    import paper_1901_08532_gb300 as nb
-    torch.cuda.set_device(0)
-    n = args.n if args.n != N_BODY else 65536
-    prec = {"mixed": nb.NB_MIXED, "fp64": nb.NB_FP64, "ex": nb.NB_EX, "sp": nb.NB_SP}[args.prec]
+    prec = {"mixed": nb.NB_MIXED, "fp64": nb.NB_FP64, "ex": nb.NB_EX, "sp": nb.NB_SP}[prec_name]
     m, x, v = ni.plummer(n, 2)
     stream = torch.cuda.current_stream()
-    # dt_max = 2^-4 so that every particle synchronises at t_end = 1/16
     ctx = nb.NBody(m, x, v, EPS, precision=prec, stream=stream, dt_max=2.0 ** -4)
     ctx.predict(0.0)
     ctx.evaluate(None, out=False)
@@ -760,7 +839,7 @@ def integrate_bench(args):
     E0 = sum(ctx.energy())
     _, i0 = ctx.counters()
     t0 = time.perf_counter()
-    steps, (lt, ln) = ctx.run_until(1.0 / 16, log_cap=10 ** 7)
+    steps, (lt, ln) = ctx.run_until(t_end, log_cap=10 ** 7)
     el = time.perf_counter() - t0
     _, i1 = ctx.counters()
     E1 = sum(ctx.energy())
@@ -769,17 +848,97 @@ def integrate_bench(args):
     flops = FLOPS_PER_INTERACTION * float(n) * n / full_s / 1e12
     peak = PEAK_FP64_TFLOPS if prec == nb.NB_FP64 else PEAK_FP32_TFLOPS
     n_fp32_ops = {nb.NB_EX: EX_OPS_PER_INTERACTION}.get(prec)
-    print(json.dumps({"workload": f"plummer_N{n}_eps1e-4_{args.prec}", "full_eval_s": full_s,
-                      "full_eval_interactions_per_s": float(n) * n / full_s,
-                      "full_eval_frac_of_peak": (flops / peak if n_fp32_ops is None else
-                                                 n_fp32_ops * float(n) * n / full_s / PEAK_FP32_OPS),
-                      "integration_t_end": 1.0 / 16, "block_steps": steps,
-                      "integration_s": el, "us_per_block_step": 1e6 * el / max(steps, 1),
-                      "integration_interactions": i1 - i0,
-                      "integration_interactions_per_s": (i1 - i0) / el,
-                      "mean_active": float(ln.mean()), "max_active": int(ln.max()),
-                      "active_log2_histogram": hist.tolist(), "energy_rel_error": abs((E1 - E0) / E0)}))
+    return {"workload": f"plummer_N{n}_eps1e-4_{prec_name}", "full_eval_s": full_s,
+            "full_eval_interactions_per_s": float(n) * n / full_s,
+            "full_eval_frac_of_peak": (flops / peak if n_fp32_ops is None else
+                                       n_fp32_ops * float(n) * n / full_s / PEAK_FP32_OPS),
+            "integration_t_end": t_end, "block_steps": steps,
+            "integration_s": el, "us_per_block_step": 1e6 * el / max(steps, 1),
+            "integration_interactions": i1 - i0,
+            "integration_interactions_per_s": (i1 - i0) / el,
+            "mean_active": float(ln.mean()), "max_active": int(ln.max()),
+            "active_log2_histogram": hist.tolist(), "energy_rel_error": abs((E1 - E0) / E0)}
+
+
+def integrate_bench(args):
+    """Plummer N = 65536 (--prec fp64 in this mode's reference config; ex and
+    mixed also run): one full-N evaluation (2^32 interactions), then
+    block-step integration to t = 1/16."""
+    import numpy as np
+    import torch
+
+    import paper_1901_08532_gb300 as nb
+    torch.cuda.set_device(0)
+    set_device_peaks(torch, 0)
+    n = args.n if args.n != N_BODY else 65536
+    print(json.dumps(integrate_run(nb, np, torch, n, args.prec)))
     return 0
+
+
+def ensemble_leg(nb, np, torch, prec_name="ex", t_end=0.25, sample=8):
+    """Batched ensemble (256 Plummer systems, N log-uniform in [256, 16384],
+    seed 4, eps 1e-4, own block steps) to t_end in one persistent
+    graph-captured launch at the library's default shape, then `sample`
+    systems spread over the size range advanced one at a time through
+    nb_run_until against the same systems as one ensemble."""
+    import nb_inputs as ni
+    prec = {"mixed": nb.NB_MIXED, "mixed32": nb.NB_MIXED32, "fp64": nb.NB_FP64, "ex": nb.NB_EX}[prec_name]
+    sizes = ni.ensemble_sizes(256, 4)
+    parts = [ni.plummer(int(k), 1000 + q) for q, k in enumerate(sizes)]
+
+    def run(idx):
+        cat = [np.concatenate([parts[k][f] for k in idx]) for f in range(3)]
+        ens = nb.Ensemble(sizes[idx], *cat, EPS, precision=prec)
+        _, it0, _ = ens.stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ens.run(t_end)
+        el = time.perf_counter() - t0
+        steps, it1, _ = ens.stats()
+        shape = ens.shape()
+        ens.close()
+        return {"seconds": el, "interactions": it1 - it0, "interactions_per_s": (it1 - it0) / el,
+                "block_steps": int(steps.sum()), "shape": list(shape)}
+
+    out = {"workload": f"ensemble_256_plummer_N256-16384_eps1e-4_{prec_name}_t{t_end:g}",
+           "systems": int(sizes.size), "particles": int(sizes.sum()), "all": run(list(range(sizes.size)))}
+    order = np.argsort(sizes)
+    idx = [int(order[q]) for q in np.linspace(0, sizes.size - 1, sample).astype(int)]
+    batched = run(idx)
+    tot_el, tot_it = 0.0, 0.0
+    for k in idx:
+        ctx = nb.NBody(*parts[k], EPS, precision=prec)
+        _, i0 = ctx.counters()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.run_until(t_end)
+        tot_el += time.perf_counter() - t0
+        _, i1 = ctx.counters()
+        tot_it += i1 - i0
+        ctx.close()
+    out["sample"] = {"sizes": [int(sizes[k]) for k in idx], "ensemble": batched,
+                     "one_at_a_time": {"seconds": tot_el, "interactions": tot_it,
+                                       "interactions_per_s": tot_it / tot_el},
+                     "speedup": batched["interactions_per_s"] / (tot_it / tot_el)}
+    return out
+
+
+def config_legs(nb, np, torch, local):
+    """The other configurations, compact, each under its own clock record:
+    the 256-system EX ensemble to t = 1/4 (with the one-at-a-time comparison
+    on 8 systems), the differentiable N = 8192 trajectory (64 steps,
+    checkpoints every 8), and the N = 65536 block-step integration to
+    t = 1/16 in EX and FP64."""
+    legs = {}
+    for name, fn in (("ensemble_ex_256", lambda: ensemble_leg(nb, np, torch, "ex")),
+                     ("adjoint_n8192", lambda: adjoint_run(torch)),
+                     ("integrate_n65536_ex", lambda: integrate_run(nb, np, torch, 65536, "ex")),
+                     ("integrate_n65536_fp64", lambda: integrate_run(nb, np, torch, 65536, "fp64"))):
+        with Clocks(local) as clk:
+            rec = fn()
+        rec["clocks"] = clk.summary()
+        legs[name] = rec
+    return legs
 
 
 def precision_study(args):
@@ -822,8 +981,64 @@ def precision_study(args):
     return 0
 
 
+def measure_peaks(nb, torch, iters=4096):
+    """Measured CUDA-core peaks of this device (nb_peak_probe): operations
+    per clock per SM and the derived whole-GPU peaks at the device's maximum
+    SM clock.  FP32 and FP64 flop peaks count an FMA as 2 flops."""
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    max_mhz = _max_sm_mhz(dev)
+    res = {"sms": sms, "sm_max_mhz": max_mhz, "kinds": {}}
+    # (label, probe kind, blocks per SM, threads): 32 warps per SM, and the
+    # three-operand case also at the 12 warps per SM the mixed kernel runs
+    for label, kind, bps, thr, it in (("ffma", "ffma", 4, 256, iters), ("ffma2", "ffma2", 4, 256, iters),
+                                      ("dfma", "dfma", 4, 256, max(1, iters // 16)),
+                                      ("rsqrt", "rsqrt", 4, 256, iters), ("rcp", "rcp", 4, 256, iters),
+                                      ("ffma2+rsqrt", "ffma2+rsqrt", 4, 256, iters),
+                                      ("ffma2+rsqrt_noftz", "ffma2+rsqrt_noftz", 4, 256, iters),
+                                      ("ffma2+rsqrt+rcp", "ffma2+rsqrt+rcp", 4, 256, iters),
+                                      ("ffma2_3reg", "ffma2_3reg", 4, 256, iters),
+                                      ("ffma2_3reg@12warps", "ffma2_3reg", 3, 128, iters)):
+        res["kinds"][label] = nb.peak_probe(kind, bps, thr, it)
+    k = res["kinds"]
+    fp32 = max(k["ffma"]["ops_per_clk_per_sm"], k["ffma2"]["ops_per_clk_per_sm"])
+    res["fp32_fma_per_clk_per_sm"] = fp32
+    res["fp64_fma_per_clk_per_sm"] = k["dfma"]["ops_per_clk_per_sm"]
+    res["fp32_tflops_at_max_clock"] = 2 * fp32 * sms * max_mhz * 1e6 / 1e12
+    res["fp64_tflops_at_max_clock"] = 2 * k["dfma"]["ops_per_clk_per_sm"] * sms * max_mhz * 1e6 / 1e12
+    return res
+
+
+def _max_sm_mhz(dev):
+    """The device's maximum SM clock (nvidia-smi clocks.max.sm), else 2070."""
+    try:
+        import torch
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+        out = subprocess.run(["nvidia-smi", f"--id={uuid}", "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=30)
+        return float(out.stdout.strip().splitlines()[0])
+    except Exception:
+        return 2070.0
+
+
+def peaks_bench(args):
+    import torch
+
+    import paper_1901_08532_gb300 as nb
+    torch.cuda.set_device(0)
+    with Clocks(0) as clk:
+        res = measure_peaks(nb, torch)
+    res["clocks"] = clk.summary()
+    print(json.dumps(res))
+    return 0
+
+
 def main():
     args = parse()
+    if args.peaks:
+        return peaks_bench(args)
     if args.precision_study:
         return precision_study(args)
     if args.integrate:

@@ -57,9 +57,9 @@ typedef enum {
     NB_ESTATE = -6      /* call out of order (e.g. correct before eval)   */
 } nb_status;
 
-/* Arithmetic of the evaluation step (section 3 item 6).  In a context
- * (nb_init) prediction, correction, time steps and energy are FP64 in every
- * mode; ensembles differ for NB_MIXED (see nb_ensemble_init). */
+/* Arithmetic of the evaluation step (section 3 item 6).  Prediction,
+ * correction, time steps and energy are FP64 in every mode, for contexts
+ * (nb_init) and ensembles, except the ensemble-only NB_MIXED32. */
 typedef enum {
     NB_FP64 = 0,  /* every operation of the pair sum in IEEE double          */
     NB_MIXED = 1, /* FP64 positions and accumulation; pair differences
@@ -71,19 +71,26 @@ typedef enum {
                      but positions rounded to FP32 (no lo part), so pair
                      differences carry the rounding of the positions; not
                      available for ensembles                                 */
-    NB_EX = 3     /* extended precision (section 3 item 6): every predicted
+    NB_EX = 3,    /* extended precision (section 3 item 6): every predicted
                      position, velocity, acceleration and mass held as a
                      double word hi + lo of FP32 numbers (about 48 mantissa
                      bits, FP32 exponent range) and the whole pair term
                      computed in double-word arithmetic from FP32
                      operations; per-tile sums added in FP64              */
+    NB_MIXED32 = 4 /* ensembles only: the NB_MIXED pair arithmetic with the
+                     predictor, the corrector's increments and the step
+                     criterion in FP32, from an FP32 copy of the state (x
+                     and v as double words); the increments are added to
+                     the FP64 state.  Faster per block step than NB_MIXED,
+                     not the form in which prediction and correction stay
+                     FP64                                                  */
 } nb_precision;
 
 /* Shape of the evaluation launch.  0 in any field means "choose
  * automatically". */
 typedef struct {
-    int32_t ki;       /* i-particles per thread: 1, 2 or 4 (mixed: 1 or 2;
-                         EX: 1)                                               */
+    int32_t ki;       /* i-particles per thread: FP64 1, 2 or 4; mixed and
+                         SP 1, 2 or 3 (3 with junroll 4); EX 1               */
     int32_t threads;  /* threads per block: 32..512, multiple of 32 (EX:
                          at most 128)                                         */
     int32_t jtile;    /* j-particles per shared-memory stage: multiple of lanes */
@@ -124,7 +131,11 @@ void nb_config_default(nb_config *cfg);
 
 /* Create a context on the current CUDA device for n particles with masses
  * m[n], positions x[n][3] and velocities v[n][3] (host arrays, copied) and
- * softening eps > 0.  Computes the starting acceleration and jerk (one
+ * softening eps > 0: the inputs the paper's device receives (section 2:
+ * the host feeds the device coordinates, velocities and masses, and the
+ * device computes the forces).  The start-up below is
+ * the initialisation of the 6th-order Hermite scheme of section 3 (opening
+ * paragraph), which needs a, jerk and snap before the first predictor.  Computes the starting acceleration and jerk (one
  * evaluation pass with a_j = 0), then the snap (a second pass using those
  * accelerations), sets crackle to zero, t_i = 0 and the starting steps
  * (eta_s * min(|a|/|j|, sqrt(|a|/|s|)), rounded down to a power of two and
@@ -163,8 +174,43 @@ nb_status nb_evaluate(nb_ctx *ctx, const int32_t *active, int64_t n_act,
                       int active_on_device, double *acc, double *jerk,
                       double *snap, int out_on_device);
 
-/* Corrector (section 3) for the particles of the last nb_evaluate, whose
- * prediction time must equal t: corrected x and v, the new a/jerk/snap,
+/* Block-step scheduler alone (section 2): t_next = min_i(t_i + dt_i) and the
+ * active set {i : t_i + dt_i == t_next}, ascending (every particle in shared
+ * mode), without predicting or evaluating.  *t_next and *n_act (may be
+ * NULL) receive them; nb_get_active copies the set out.  Together with
+ * nb_predict, nb_evaluate_partial, nb_set_forces and nb_correct this is
+ * nb_step taken apart, for a caller that sums the evaluation over several
+ * devices. */
+nb_status nb_schedule(nb_ctx *ctx, double *t_next, int64_t *n_act);
+
+/* Evaluation of the active set (as in nb_evaluate) against the predicted
+ * j-particles of [j_lo, j_hi) only: one device's share of the paper's
+ * multi-device evaluation (section 3 item 3: with n devices each evaluates
+ * N (N/n) interactions, and the results are collected and reduced).  The
+ * self term needs no special care (eps > 0 makes it exactly 0 wherever i
+ * falls).  part receives the FP64 partial sums [9][n_act] (row q * n_act + k:
+ * acc x, y, z, jerk x, y, z, snap x, y, z of active[k]), a device pointer
+ * when part_on_device != 0, else a host pointer (the call then
+ * synchronises).  The partial sums are not kept for nb_correct: add the
+ * shares of all j-ranges and load the totals with nb_set_forces.  Shares
+ * that cover [0, n) add up, to rounding, to nb_evaluate's sums.
+ * Errors: NB_EINVAL (not 0 <= j_lo <= j_hi <= n; for NB_MIXED, NB_SP and
+ * NB_EX j_lo and j_hi must be multiples of 4, or j_hi == n; as nb_evaluate),
+ * NB_ESTATE (no prediction yet). */
+nb_status nb_evaluate_partial(nb_ctx *ctx, const int32_t *active, int64_t n_act, int active_on_device,
+                              int64_t j_lo, int64_t j_hi, double *part, int part_on_device);
+
+/* Load the acceleration, jerk and snap of the active set (f: [9][n_act]
+ * doubles in the layout of nb_evaluate_partial, device or host per
+ * f_on_device) as the evaluation at the last prediction time, so that
+ * nb_correct can follow.  Errors: NB_EINVAL, NB_ENONFINITE (a non-finite
+ * host value), NB_ESTATE (no prediction yet). */
+nb_status nb_set_forces(nb_ctx *ctx, const int32_t *active, int64_t n_act, int active_on_device,
+                        const double *f, int f_on_device);
+
+/* Corrector (section 3) for the particles of the last nb_evaluate (or
+ * nb_set_forces), whose prediction time must equal t: corrected x and v, the
+ * new a/jerk/snap,
  * crackle from quintic interpolation, t_i = t and a new step (generalised
  * Aarseth criterion, section 3 item 3, which sets no bound when every
  * derivative is zero; shared step when dt_shared > 0).
@@ -172,14 +218,18 @@ nb_status nb_evaluate(nb_ctx *ctx, const int32_t *active, int64_t n_act,
  * value is not finite). */
 nb_status nb_correct(nb_ctx *ctx, double t);
 
-/* One block step, entirely on the device: t_next = min_i(t_i + dt_i), the
- * active set {i : t_i + dt_i == t_next} (ascending indices), predict all,
+/* One block step (section 2: individual power-of-two block time steps;
+ * section 3, opening paragraph: the predictor, evaluation and corrector
+ * stages, in that order), entirely on the device: t_next = min_i(t_i + dt_i),
+ * the active set {i : t_i + dt_i == t_next} (ascending indices), predict all,
  * evaluate the active set, correct it.  *t_out and *n_act_out (either may
  * be NULL) receive the step's time and active count. */
 nb_status nb_step(nb_ctx *ctx, double *t_out, int64_t *n_act_out);
 
-/* Block steps until every particle has reached t_end (a multiple of dt_max,
- * so that all particles synchronise there).  *steps_out may be NULL.
+/* Block steps (section 2; the stages of section 3, and the time-step
+ * selection of section 3 item 3 after every corrector) until every particle
+ * has reached t_end (a multiple of dt_max, so that all particles synchronise
+ * there).  *steps_out may be NULL.
  * When log_cap > 0, the first log_cap steps are recorded in log_t[] (time)
  * and log_n[] (active count). */
 nb_status nb_run_until(nb_ctx *ctx, double t_end, int64_t *steps_out,
@@ -214,12 +264,19 @@ nb_status nb_energy(nb_ctx *ctx, double *ekin, double *epot);
 nb_status nb_angmom(nb_ctx *ctx, double L[3], double *labs);
 
 /* Copy the integrator state to host arrays ([n][3] for vectors, [n] for t
- * and dt); any pointer may be NULL to skip that field.  c is the crackle. */
+ * and dt); any pointer may be NULL to skip that field.  c is the crackle.
+ * This is the state of the Hermite scheme of section 3 (positions,
+ * velocities, a, jerk, snap, crackle, own time and block step, section 2).
+ * In section 3 item 3 particle data crosses between host and device at
+ * every shared step; here the state stays in device memory and this call
+ * copies it out on request.
+ * nb_get_state followed by nb_set_state on a fresh context (start_forces =
+ * 0) resumes an integration bit for bit. */
 nb_status nb_get_state(nb_ctx *ctx, double *x, double *v, double *a, double *j,
                        double *s, double *c, double *t, double *dt);
 
-/* Overwrite the integrator state from host arrays (checkpoint resume);
- * NULL skips a field.  Errors: NB_ENONFINITE, NB_EINVAL (dt not a power of
+/* Overwrite the integrator state from host arrays (checkpoint resume of the
+ * section 3 Hermite state, see nb_get_state); NULL skips a field.  Errors: NB_ENONFINITE, NB_EINVAL (dt not a power of
  * two in [dt_min, dt_max], or t_i not a multiple of dt_i). */
 nb_status nb_set_state(nb_ctx *ctx, const double *x, const double *v,
                        const double *a, const double *j, const double *s,
@@ -265,10 +322,10 @@ typedef struct nb_ensemble nb_ensemble;
  * and steps are always computed, in one launch).  The ensemble runs on
  * cfg->stream, or on a stream of its own when that is NULL (graph capture
  * needs a stream other than the legacy default stream).  Precision NB_FP64,
- * NB_MIXED or NB_EX (NB_SP is rejected).  NB_MIXED ensembles also run the
- * predictor (from an FP32 copy of the state, x and v as double words) and
- * the corrector's increments and step criterion in FP32; NB_FP64 and NB_EX
- * use the FP64 predictor and corrector.
+ * NB_MIXED, NB_EX or NB_MIXED32 (NB_SP is rejected).  NB_FP64, NB_MIXED and
+ * NB_EX use the FP64 predictor and corrector, as a context does; NB_MIXED32
+ * runs the predictor (from an FP32 copy of the state, x and v as double
+ * words) and the corrector's increments and step criterion in FP32.
  * Errors: NB_EINVAL, NB_ENONFINITE, NB_ENOMEM, NB_ECUDA. */
 nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *sizes,
                            const double *m, const double *x, const double *v, double eps,
@@ -278,7 +335,7 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
  * 8 the non-portable cluster size, NB_EINVAL from nb_ensemble_run where the
  * device cannot co-schedule it), threads per block (64..256, multiple of 32),
  * j-tile length (multiple of 4, at most 1024).  0 in a field selects the
- * default: NB_MIXED 4 blocks, j-tile 1024; NB_FP64 and NB_EX 16 blocks where
+ * default: NB_MIXED and NB_MIXED32 4 blocks, j-tile 1024; NB_FP64 and NB_EX 16 blocks where
  * the device co-schedules clusters of 16, else 8, j-tile 256; 128 threads. */
 nb_status nb_ensemble_set_shape(nb_ensemble *e, int32_t ctas_per_system, int32_t threads,
                                 int32_t jtile);
@@ -301,6 +358,26 @@ nb_status nb_ensemble_get_state(nb_ensemble *e, double *x, double *v, double *a,
  * NULL), pair interactions evaluated since creation, and launches issued. */
 nb_status nb_ensemble_stats(nb_ensemble *e, int64_t *steps, double *interactions,
                             int64_t *launches);
+
+/* Record every block step the ensemble takes from now on (in this and later
+ * nb_ensemble_run calls), the ensemble form of nb_run_until's log (section 2
+ * block steps): per step its system, time and active count, and the active
+ * particles' indices within their system, ascending.  step_cap steps and
+ * idx_cap indices are kept in device memory allocated here; steps beyond
+ * either capacity are counted but not kept.  step_cap = idx_cap = 0 turns
+ * the log off and frees it.  Calling this resets the log.
+ * Errors: NB_EINVAL (a capacity < 0, step_cap > 2^32, idx_cap > 2^34),
+ * NB_ENOMEM, NB_ECUDA. */
+nb_status nb_ensemble_set_log(nb_ensemble *e, int64_t step_cap, int64_t idx_cap);
+
+/* Copy the step log out.  Host arrays with room for the capacities given to
+ * nb_ensemble_set_log (any may be NULL): sys[k], t[k], n_act[k] and
+ * idx_off[k] per kept step k (idx_off: where step k's indices start in
+ * idx[], -1 where they were not kept), the steps of each system in the
+ * order taken (steps of different systems interleave).  *n_steps and *n_idx
+ * (may be NULL) receive the totals recorded, kept or not. */
+nb_status nb_ensemble_get_log(nb_ensemble *e, int32_t *sys, double *t, int32_t *n_act,
+                              int64_t *idx_off, int32_t *idx, int64_t *n_steps, int64_t *n_idx);
 
 /* Message for the last error of e (NULL: the last failed nb_ensemble_init
  * on this thread). */
@@ -337,6 +414,45 @@ nb_status nb_pairs_fp64_adjoint(int64_t n, const double *m, const double *x, con
                                 const double *gjerk, const double *gsnap, double *gx, double *gv,
                                 double *ga, double *gm, void *stream);
 
+/* The O(N) stages of a fixed-step Hermite trajectory (section 3: predictor
+ * and corrector around the evaluation; every particle on the shared step of
+ * section 3 item 3) and their adjoints, for differentiating trajectories.
+ * All arrays are device [n][3] doubles; work is only enqueued on `stream`;
+ * h > 0 is the step (in [1e-12, 1e6]).  Errors: NB_EINVAL (n outside
+ * [1, 2^40], bad h, a required pointer NULL), NB_ECUDA.
+ *
+ * Predictor: xp, vp, ap of every particle from x, v, a, jerk j, snap s and
+ * crackle c over the step h (Taylor series through crackle). */
+nb_status nb_traj_predict(int64_t n, double h, const double *x, const double *v, const double *a,
+                          const double *j, const double *s, const double *c, double *xp, double *vp,
+                          double *ap, void *stream);
+
+/* Adjoint of nb_traj_predict: cotangents gxp, gvp, gap of its outputs (NULL
+ * = zero) are ADDED to gx, gv, ga, gj, gs, and gc is WRITTEN (the crackle
+ * enters the step only through the predictor). */
+nb_status nb_traj_predict_adjoint(int64_t n, double h, const double *gxp, const double *gvp,
+                                  const double *gap, double *gx, double *gv, double *ga, double *gj,
+                                  double *gs, double *gc, void *stream);
+
+/* Corrector: from the start-of-step x, v, a, j, s and the new acceleration,
+ * jerk and snap A, J, S (the evaluation at the predicted state) the
+ * corrected x1, v1 (two-point Hermite quadrature, v first) and the crackle
+ * c1 of the quintic through (a, j, s) and (A, J, S), exactly as nb_correct
+ * applies them. */
+nb_status nb_traj_correct(int64_t n, double h, const double *x, const double *v, const double *a,
+                          const double *j, const double *s, const double *A, const double *J,
+                          const double *S, double *x1, double *v1, double *c1, void *stream);
+
+/* Adjoint of nb_traj_correct: from the cotangents gx1, gv1, gc1 of its
+ * outputs and gA_in, gJ_in, gS_in of A, J, S's other uses (any may be NULL
+ * = zero) it WRITES the gradients gx, gv, ga, gj, gs of the start-of-step
+ * state and the total cotangents gA, gJ, gS of the evaluation's outputs
+ * (the input of nb_pairs_fp64_adjoint). */
+nb_status nb_traj_correct_adjoint(int64_t n, double h, const double *gx1, const double *gv1,
+                                  const double *gc1, const double *gA_in, const double *gJ_in,
+                                  const double *gS_in, double *gx, double *gv, double *ga, double *gj,
+                                  double *gs, double *gA, double *gJ, double *gS, void *stream);
+
 /* Allocation-free FP64 evaluation.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory: a host
  * application that owns all GPU memory through its own pool or caching
@@ -364,12 +480,38 @@ nb_status nb_pairs_fp64_adjoint(int64_t n, const double *m, const double *x, con
  * GPU (other streams, other threads) race on it and must be serialised.
  * A device-side wait that times out leaves out incomplete; this entry
  * point does not report it.
- * Errors (message via nb_last_error(NULL)): NB_EINVAL (bad argument, or an
- * explicit split whose partials, split * 9 * n_act doubles, exceed the
- * scratch), NB_ECUDA. */
+ * Errors (message via nb_last_error(NULL)): NB_EINVAL (bad argument; jrec
+ * not 16-byte, active not 4-byte or out not 8-byte aligned; an explicit
+ * split whose partials, split * 9 * n_act doubles, exceed the scratch, or
+ * that needs more than 4096 i-tiles or 65535 j-chunks), NB_ECUDA.  Every
+ * NB_EINVAL is returned before any CUDA call, so nothing is launched. */
 nb_status nb_evaluate_fp64_static(const void *jrec, int64_t n, const int32_t *active,
                                   int64_t n_act, double eps, int32_t split, double *out,
                                   void *stream);
+
+/* Throughput probe of one CUDA-core pipe on the current device, the
+ * measured denominator of the evaluation kernels' roofline (the pair sum of
+ * section 3 item 4 runs on these pipes, not on tensor cores).  kind:
+ *   0 scalar FP32 FMA, 1 packed f32x2 FMA, 2 FP64 FMA, 3 R^(-1/2) estimate,
+ *   4 1/R estimate, 5 packed FMAs with one R^(-1/2) estimate per 13 (the
+ *   proportion of the mixed pair term), 6 the same with the estimate in its
+ *   non-flushing form, 7 packed FMAs with one R^(-1/2) and one 1/R estimate
+ *   per 13, 8 packed FMAs each reading three distinct register pairs (no
+ *   loop constants).
+ * The probe launches blocks_per_sm blocks of `threads` threads on every SM
+ * (all resident at once), each thread running `iters` iterations of
+ * independent dependency chains, once to warm up and once timed; it
+ * allocates and frees a few KB and synchronises.  Outputs (any may be NULL):
+ * operations per clock per SM from the blocks' own cycle counts (an FMA is
+ * one operation, an f32x2 FMA two), estimates per clock per SM (kinds 5-7;
+ * kinds 3-4 report theirs as operations), operations per second over the
+ * GPU from CUDA events, and the SM clock in MHz the launch ran at.
+ * Errors: NB_EINVAL (kind outside 0..8, blocks_per_sm outside 1..32,
+ * threads not a multiple of 32 in 32..1024, iters outside 1..2^24),
+ * NB_ECUDA (message via nb_last_error(NULL)). */
+nb_status nb_peak_probe(int32_t kind, int32_t blocks_per_sm, int32_t threads, int32_t iters,
+                        double *ops_per_clk_sm, double *ops_per_s, double *est_per_clk_sm,
+                        double *sm_mhz);
 
 /* Message for the last error of ctx ("" if none).  ctx may be NULL, then
  * the message of the last failed nb_init on this thread is returned. */

@@ -29,7 +29,7 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 NB_OK, NB_EINVAL, NB_ECUDA, NB_ENOMEM, NB_ENONFINITE, NB_ETIMEOUT, NB_ESTATE = 0, -1, -2, -3, -4, -5, -6
-NB_FP64, NB_MIXED, NB_SP, NB_EX = 0, 1, 2, 3
+NB_FP64, NB_MIXED, NB_SP, NB_EX, NB_MIXED32 = 0, 1, 2, 3, 4
 _STATUS = {NB_EINVAL: "NB_EINVAL", NB_ECUDA: "NB_ECUDA", NB_ENOMEM: "NB_ENOMEM",
            NB_ENONFINITE: "NB_ENONFINITE", NB_ETIMEOUT: "NB_ETIMEOUT", NB_ESTATE: "NB_ESTATE"}
 
@@ -67,6 +67,9 @@ _lib.nb_predict.argtypes = [_vp, C.c_double]
 _lib.nb_get_predicted.argtypes = [_vp, _d, _d, _d]
 _lib.nb_evaluate.argtypes = [_vp, _vp, C.c_int64, C.c_int, _vp, _vp, _vp, C.c_int]
 _lib.nb_correct.argtypes = [_vp, C.c_double]
+_lib.nb_schedule.argtypes = [_vp, _d, _i64]
+_lib.nb_evaluate_partial.argtypes = [_vp, _vp, C.c_int64, C.c_int, C.c_int64, C.c_int64, _vp, C.c_int]
+_lib.nb_set_forces.argtypes = [_vp, _vp, C.c_int64, C.c_int, _vp, C.c_int]
 _lib.nb_step.argtypes = [_vp, _d, _i64]
 _lib.nb_run_until.argtypes = [_vp, C.c_double, _i64, C.c_int64, _d, _i64]
 _lib.nb_run_diag.argtypes = [_vp, C.c_double, C.c_double, C.c_int64, _d, _i64, _i64]
@@ -90,12 +93,14 @@ _lib.nb_ensemble_get_shape.argtypes = [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_
 _lib.nb_ensemble_run.argtypes = [_vp, C.c_double, C.c_int]
 _lib.nb_ensemble_get_state.argtypes = [_vp] + [_d] * 8
 _lib.nb_ensemble_stats.argtypes = [_vp, _i64, _d, _i64]
+_lib.nb_ensemble_set_log.argtypes = [_vp, C.c_int64, C.c_int64]
+_lib.nb_ensemble_get_log.argtypes = [_vp, _i32, _d, _i32, _i64, _i32, _i64, _i64]
 _lib.nb_ensemble_last_error.argtypes = [_vp]
 _lib.nb_ensemble_last_error.restype = C.c_char_p
 _lib.nb_ensemble_free.argtypes = [_vp]
 _lib.nb_ensemble_free.restype = None
 for _f in ("nb_ensemble_init", "nb_ensemble_set_shape", "nb_ensemble_get_shape", "nb_ensemble_run",
-           "nb_ensemble_get_state", "nb_ensemble_stats"):
+           "nb_ensemble_get_state", "nb_ensemble_stats", "nb_ensemble_set_log", "nb_ensemble_get_log"):
     getattr(_lib, _f).restype = C.c_int
 _lib.nb_pairs_workspace_bytes.argtypes = [C.c_int64]
 _lib.nb_pairs_workspace_bytes.restype = C.c_size_t
@@ -104,24 +109,38 @@ _lib.nb_pairs_fp64.restype = C.c_int
 _lib.nb_pairs_fp64_adjoint.argtypes = [C.c_int64, _vp, _vp, _vp, _vp, C.c_double, _vp, _vp, _vp,
                                        _vp, _vp, _vp, _vp, _vp]
 _lib.nb_pairs_fp64_adjoint.restype = C.c_int
+_lib.nb_traj_predict.argtypes = [C.c_int64, C.c_double] + [_vp] * 9 + [_vp]
+_lib.nb_traj_predict_adjoint.argtypes = [C.c_int64, C.c_double] + [_vp] * 9 + [_vp]
+_lib.nb_traj_correct.argtypes = [C.c_int64, C.c_double] + [_vp] * 11 + [_vp]
+_lib.nb_traj_correct_adjoint.argtypes = [C.c_int64, C.c_double] + [_vp] * 14 + [_vp]
+for _f in ("nb_traj_predict", "nb_traj_predict_adjoint", "nb_traj_correct", "nb_traj_correct_adjoint"):
+    getattr(_lib, _f).restype = C.c_int
+_lib.nb_peak_probe.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _d, _d, _d, _d]
+_lib.nb_peak_probe.restype = C.c_int
 _lib.nb_last_error.argtypes = [_vp]
 _lib.nb_last_error.restype = C.c_char_p
 _lib.nb_free.argtypes = [_vp]
 _lib.nb_free.restype = None
 for _f in ("nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_correct", "nb_step", "nb_run_until",
+           "nb_schedule", "nb_evaluate_partial", "nb_set_forces",
            "nb_run_diag",
            "nb_energy", "nb_angmom", "nb_get_state", "nb_set_state", "nb_get_active",
            "nb_set_tiles", "nb_resolve_tiles", "nb_counters"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("nb_config_default", "nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_correct", "nb_step",
+            "nb_schedule", "nb_evaluate_partial", "nb_set_forces",
             "nb_run_until", "nb_run_diag", "nb_energy", "nb_angmom", "nb_get_state", "nb_set_state",
             "nb_get_active", "nb_set_tiles", "nb_resolve_tiles", "nb_counters", "nb_inject_fault",
             "nb_evaluate_fp64_static", "nb_last_error", "nb_free", "nb_ensemble_init",
             "nb_ensemble_set_shape", "nb_ensemble_get_shape", "nb_ensemble_run", "nb_ensemble_get_state",
-            "nb_ensemble_stats",
+            "nb_ensemble_stats", "nb_ensemble_set_log", "nb_ensemble_get_log",
             "nb_ensemble_last_error", "nb_ensemble_free", "nb_pairs_workspace_bytes", "nb_pairs_fp64",
-            "nb_pairs_fp64_adjoint")
+            "nb_pairs_fp64_adjoint", "nb_traj_predict", "nb_traj_predict_adjoint", "nb_traj_correct",
+            "nb_traj_correct_adjoint", "nb_peak_probe")
+
+PROBE_KINDS = ("ffma", "ffma2", "dfma", "rsqrt", "rcp", "ffma2+rsqrt", "ffma2+rsqrt_noftz",
+               "ffma2+rsqrt+rcp", "ffma2_3reg")
 
 
 def lib():
@@ -152,6 +171,22 @@ def _stream_handle(stream):
 
 def _is_torch(x):
     return type(x).__module__.startswith("torch")
+
+
+def peak_probe(kind, blocks_per_sm=4, threads=256, iters=4096):
+    """Throughput of one CUDA-core pipe on the current device (nb_peak_probe):
+    kind is a name from PROBE_KINDS or its index.  Returns a dict with
+    operations per clock per SM (FMA = 1 operation; an f32x2 FMA = 2),
+    special-function estimates per clock per SM (mixed kinds), operations
+    per second over the whole GPU, and the SM clock the launch ran at."""
+    k = PROBE_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    per_clk, per_s, est, mhz = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    st = _lib.nb_peak_probe(k, int(blocks_per_sm), int(threads), int(iters), C.byref(per_clk),
+                            C.byref(per_s), C.byref(est), C.byref(mhz))
+    if st != NB_OK:
+        raise NBError(st, _lib.nb_last_error(None).decode())
+    return {"kind": PROBE_KINDS[k], "ops_per_clk_per_sm": per_clk.value,
+            "est_per_clk_per_sm": est.value, "ops_per_s": per_s.value, "sm_mhz": mhz.value}
 
 
 class NBody:
@@ -248,6 +283,51 @@ class NBody:
 
     def correct(self, t):
         self._check(_lib.nb_correct(self._ctx, float(t)))
+
+    # --- the block step taken apart (multi-device evaluation) --------------
+    def schedule(self):
+        """Next block time and active count (nb_schedule); active() lists the set."""
+        t = C.c_double()
+        na = C.c_int64()
+        self._check(_lib.nb_schedule(self._ctx, C.byref(t), C.byref(na)))
+        return t.value, int(na.value)
+
+    @staticmethod
+    def _active_arg(active, n):
+        if active is None:
+            return None, n, 0, None
+        if _is_torch(active) and active.is_cuda:
+            return active.data_ptr(), active.numel(), 1, active
+        active = np.ascontiguousarray(active, dtype=np.int32)
+        return active.ctypes.data, active.size, 0, active
+
+    def evaluate_partial(self, active, j_lo, j_hi, out="device"):
+        """FP64 partial sums [9, n_act] of the active set against predicted
+        j in [j_lo, j_hi) (nb_evaluate_partial): a CUDA tensor (out="device")
+        or a numpy array (out="host")."""
+        aptr, n_act, on_dev, keep = self._active_arg(active, self.n)
+        if out == "device":
+            import torch
+            part = torch.empty((9, n_act), dtype=torch.float64, device="cuda")
+            pptr, pdev = part.data_ptr(), 1
+        else:
+            part = np.empty((9, n_act))
+            pptr, pdev = part.ctypes.data, 0
+        self._check(_lib.nb_evaluate_partial(self._ctx, aptr, n_act, on_dev, int(j_lo), int(j_hi),
+                                             pptr, pdev))
+        return part
+
+    def set_forces(self, active, f):
+        """Load a, jerk, snap [9, n_act] (CUDA tensor or host array) of the
+        active set as the evaluation for correct() (nb_set_forces)."""
+        aptr, n_act, on_dev, keep = self._active_arg(active, self.n)
+        if _is_torch(f) and f.is_cuda:
+            assert f.dtype.__str__() == "torch.float64" and f.is_contiguous()
+            fptr, fdev = f.data_ptr(), 1
+        else:
+            f = np.ascontiguousarray(f, dtype=np.float64)
+            fptr, fdev = f.ctypes.data, 0
+        self._check(_lib.nb_set_forces(self._ctx, aptr, n_act, on_dev, fptr, fdev))
 
     # --- integration --------------------------------------------------------
     def step(self):
@@ -407,6 +487,32 @@ class Ensemble:
         self._check(_lib.nb_ensemble_stats(self._e, steps.ctypes.data_as(_i64), C.byref(it),
                                            C.byref(la)))
         return steps, float(it.value), int(la.value)
+
+    def set_log(self, step_cap, idx_cap):
+        """Record every block step from now on (step_cap steps, idx_cap active
+        indices kept); 0, 0 turns the log off."""
+        self._log_caps = (int(step_cap), int(idx_cap))
+        self._check(_lib.nb_ensemble_set_log(self._e, int(step_cap), int(idx_cap)))
+
+    def log(self):
+        """The step log per system: {system: [(t, active indices within the
+        system or None if not kept), ...]} in the order the steps were taken,
+        and the totals (steps, indices) recorded."""
+        sc, ic = getattr(self, "_log_caps", (0, 0))
+        sys_ = np.zeros(max(1, sc), dtype=np.int32)
+        t = np.zeros(max(1, sc))
+        na = np.zeros(max(1, sc), dtype=np.int32)
+        off = np.zeros(max(1, sc), dtype=np.int64)
+        idx = np.zeros(max(1, ic), dtype=np.int32)
+        ns, ni = C.c_int64(), C.c_int64()
+        self._check(_lib.nb_ensemble_get_log(self._e, sys_.ctypes.data_as(_i32), _ptr(t),
+                                             na.ctypes.data_as(_i32), off.ctypes.data_as(_i64),
+                                             idx.ctypes.data_as(_i32), C.byref(ns), C.byref(ni)))
+        out = {}
+        for k in range(min(sc, int(ns.value))):
+            rec = idx[off[k]:off[k] + na[k]].copy() if off[k] >= 0 else None
+            out.setdefault(int(sys_[k]), []).append((float(t[k]), rec))
+        return out, (int(ns.value), int(ni.value))
 
     def close(self):
         if getattr(self, "_e", None) and self._e.value:

@@ -1,15 +1,15 @@
 """Differentiable fixed-step 6th-order Hermite trajectories on the GPU.
 
-`PairSums` is a torch.autograd.Function whose forward is the library's FP64
-all-pairs evaluation (acceleration, jerk and snap, paper section 3 item 4)
-and whose backward is the library's hand-written adjoint kernel
-(nb_pairs_fp64 / nb_pairs_fp64_adjoint through the C-ABI).  The trajectory
-around it (predictor, corrector, quintic interpolation with a shared
-power-of-two step, the scheme of section 3 with every particle active as in
-the paper's shared time step) is written with torch tensor operations on the
-device, so torch's autograd carries the gradient through those linear
-stages, and `torch.utils.checkpoint` keeps only every `checkpoint`-th state,
-recomputing each segment in the backward pass.
+`HermiteStep` is one shared step of the scheme of section 3 (predictor,
+evaluation of acceleration, jerk and snap, corrector with the quintic
+interpolation's crackle; every particle active, as in the paper's shared
+time step) as a torch.autograd.Function: its forward runs the library's
+predictor, FP64 all-pairs evaluation and corrector kernels, and its backward
+the library's hand-written adjoints of the three (nb_traj_correct_adjoint,
+nb_pairs_fp64_adjoint, nb_traj_predict_adjoint) through the C-ABI; torch
+only allocates the tensors.  `PairSums` is the evaluation alone (used for
+the start-up).  `torch.utils.checkpoint` keeps only every
+`checkpoint`-th state, recomputing each segment in the backward pass.
 """
 from __future__ import annotations
 
@@ -78,6 +78,52 @@ class PairSums(torch.autograd.Function):
         return gm, gx, gv, ga, None
 
 
+class HermiteStep(torch.autograd.Function):
+    """One shared step of length h: (x, v, a, j, s, c) -> (x1, v1, A, J, S, c1)
+    with m [n] and the state [n, 3], FP64 CUDA tensors."""
+
+    @staticmethod
+    def forward(ctx, m, x, v, a, j, s, c, eps, h):
+        ctx.set_materialize_grads(False)
+        m, x, v, a, j, s, c = (t.contiguous() for t in (m, x, v, a, j, s, c))
+        n = m.numel()
+        stream = C.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+        xp, vp, ap = (torch.empty_like(x) for _ in range(3))
+        _check(lib().nb_traj_predict(n, float(h), *[_ptr(t) for t in (x, v, a, j, s, c, xp, vp, ap)],
+                                     stream))
+        A, J, S = (torch.empty_like(x) for _ in range(3))
+        _check(lib().nb_pairs_fp64(n, _ptr(m), _ptr(xp), _ptr(vp), _ptr(ap), float(eps), _ptr(A),
+                                   _ptr(J), _ptr(S), _ptr(_workspace(n, x.device)), stream))
+        x1, v1, c1 = (torch.empty_like(x) for _ in range(3))
+        _check(lib().nb_traj_correct(n, float(h), *[_ptr(t) for t in (x, v, a, j, s, A, J, S, x1, v1,
+                                                                        c1)], stream))
+        ctx.save_for_backward(m, xp, vp, ap)
+        ctx.eps, ctx.h = eps, h
+        return x1, v1, A, J, S, c1
+
+    @staticmethod
+    def backward(ctx, gx1, gv1, gA, gJ, gS, gc1):
+        m, xp, vp, ap = ctx.saved_tensors
+        n = m.numel()
+        h = float(ctx.h)
+        stream = C.c_void_p(torch.cuda.current_stream(xp.device).cuda_stream)
+        opt = lambda t: None if t is None else _ptr(t.contiguous())  # noqa: E731  (None = zero)
+        keep = [t.contiguous() for t in (gx1, gv1, gc1, gA, gJ, gS) if t is not None]  # noqa: F841
+        gx, gv, ga, gj, gs, gAt, gJt, gSt = (torch.empty_like(xp) for _ in range(8))
+        _check(lib().nb_traj_correct_adjoint(n, h, opt(gx1), opt(gv1), opt(gc1), opt(gA), opt(gJ),
+                                             opt(gS), *[_ptr(t) for t in (gx, gv, ga, gj, gs, gAt, gJt,
+                                                                          gSt)], stream))
+        gxp, gvp, gap = (torch.empty_like(xp) for _ in range(3))
+        gm = torch.empty_like(m)
+        _check(lib().nb_pairs_fp64_adjoint(n, _ptr(m), _ptr(xp), _ptr(vp), _ptr(ap), float(ctx.eps),
+                                           _ptr(gAt), _ptr(gJt), _ptr(gSt), _ptr(gxp), _ptr(gvp),
+                                           _ptr(gap), _ptr(gm), stream))
+        gc = torch.empty_like(xp)
+        _check(lib().nb_traj_predict_adjoint(n, h, _ptr(gxp), _ptr(gvp), _ptr(gap), _ptr(gx), _ptr(gv),
+                                             _ptr(ga), _ptr(gj), _ptr(gs), _ptr(gc), stream))
+        return gm, gx, gv, ga, gj, gs, gc, None, None
+
+
 def start_state(m, x, v, eps):
     """a and jerk from a pass with zero accelerations, snap from a pass with
     those accelerations, crackle zero (the scheme's start-up)."""
@@ -89,18 +135,7 @@ def start_state(m, x, v, eps):
 
 def hermite_step(m, eps, h, x, v, a, j, s, c):
     """One shared step of length h: predict all, evaluate all, correct."""
-    h2, h3 = h / 2.0, h / 3.0
-    xp = x + h * (v + h2 * (a + h3 * (j + (h / 4.0) * (s + (h / 5.0) * c))))
-    vp = v + h * (a + h2 * (j + h3 * (s + (h / 4.0) * c)))
-    ap = a + h * (j + h2 * (s + h3 * c))
-    A, J, S = PairSums.apply(m, xp, vp, ap, eps)
-    v1 = v + h2 * (a + A) - (h * h / 10.0) * (J - j) + (h ** 3 / 120.0) * (s + S)
-    x1 = x + h2 * (v + v1) - (h * h / 10.0) * (A - a) + (h ** 3 / 120.0) * (j + J)
-    R1 = A - a - h * j - (h * h / 2.0) * s
-    R2 = h * (J - j - h * s)
-    R3 = h * h * (S - s)
-    c1 = (60.0 * R1 - 36.0 * R2 + 9.0 * R3) / h ** 3
-    return x1, v1, A, J, S, c1
+    return HermiteStep.apply(m, x, v, a, j, s, c, eps, h)
 
 
 def trajectory(m, x0, v0, eps, h, steps, checkpoint_every=8):

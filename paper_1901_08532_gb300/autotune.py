@@ -22,7 +22,7 @@ import json
 import math
 import os
 
-MIXED_SPACE = {"ki": (1, 2), "junroll": (2, 4), "threads": (64, 128, 256), "jtile": (256, 512)}
+MIXED_SPACE = {"ki": (1, 2, 3), "junroll": (2, 4), "threads": (64, 128, 256), "jtile": (256, 512)}
 FP64_SPACE = {"ki": (1, 2), "threads": (64, 128, 256), "jtile": (128, 256)}
 EX_SPACE = {"ki": (1,), "junroll": (1, 2), "threads": (64, 128), "jtile": (256, 512, 1024)}
 
@@ -38,7 +38,9 @@ def candidates(precision: int):
     keys = sorted(space)
     for vals in itertools.product(*(space[k] for k in keys)):
         shape = dict(zip(keys, vals))
-        if precision in (1, 2) and shape["ki"] == 2 and shape["threads"] > 128:
+        if precision in (1, 2) and shape["ki"] >= 2 and shape["threads"] > 128:
+            continue
+        if precision in (1, 2) and shape["ki"] == 3 and shape["junroll"] != 4:
             continue
         if shape["ki"] == 2 and shape["threads"] > 256:
             continue

@@ -19,9 +19,11 @@
 //             active particles against all of the system's particles, j-tiles
 //             by TMA bulk copy into shared memory;
 //   correct   the owner (small sets) or the evaluating CTA (larger sets).
-// Precisions (kernel template PR): FP64 (0); mixed (1), whose predictor and
-// corrector run from an FP32 copy of the state; EX double words (2) with the
-// FP64 predictor and corrector.
+// Precisions (kernel template PR): FP64 (0); mixed (1): FP32 pair arithmetic
+// with the FP64 predictor and corrector; EX double words (2) with the FP64
+// predictor and corrector; mixed with an FP32 state copy (3): the mixed pair
+// arithmetic, with the predictor, the corrector's increments and the step
+// criterion in FP32 from an FP32 copy of the state.
 // Phases are separated by the cluster barrier (a hardware barrier with
 // release/acquire semantics at cluster scope, no flag spinning).  Systems are
 // independent, so no grid-wide synchronisation exists.  The only waits that
@@ -55,7 +57,13 @@ struct nb_ensemble {
     double *m = nullptr, *st = nullptr, *t = nullptr, *dt = nullptr, *anew = nullptr;
     double2 *jb64 = nullptr;
     float *jf32 = nullptr;
-    float *st32 = nullptr;  // mixed: FP32 copy of the state [24][P] (rows: see predict_one_mixed)
+    float *st32 = nullptr;  // NB_MIXED32: FP32 copy of the state [24][P] (rows: see predict_one_mixed)
+    // optional step log (nb_ensemble_set_log): counters [2] = steps, indices
+    unsigned long long *log_cnt = nullptr;
+    int32_t *log_sys = nullptr, *log_n = nullptr, *log_idx = nullptr;
+    double *log_t = nullptr;
+    int64_t *log_off = nullptr;
+    int64_t log_cap = 0, idx_cap = 0;
     int32_t *act = nullptr;
     int *queue = nullptr;
     int64_t *steps = nullptr;
@@ -89,6 +97,11 @@ struct EnsArgs {
     int64_t *steps;
     unsigned long long *inter;
     nb_ctl *ctl;
+    unsigned long long *log_cnt;   // NULL: no step log
+    int32_t *log_sys, *log_n, *log_idx;
+    double *log_t;
+    int64_t *log_off;
+    long long log_cap, idx_cap;
     double t_end, eps2, eta, eta_s, dt_min, dt_max, dt_shared;
     int mode;  // 0: block steps to t_end, 1: start-up (a, jerk, snap, starting steps)
     int jtile;
@@ -201,15 +214,38 @@ __device__ __forceinline__ void store_xv32(const EnsArgs &a, int i, int k, doubl
     a.st32[(21 + k) * P + i] = __double2float_rn(v - static_cast<double>(vh));
 }
 
+// The mixed j-record of particle i predicted to tp.  NB_MIXED (PR 1): the
+// FP64 Taylor predictor, as in a single-system context, then x rounded to a
+// hi + lo pair of FP32 numbers and v, a to FP32.  NB_MIXED32 (PR 3): the
+// FP32 predictor from the FP32 state copy.
+template <int PR>
+__device__ __forceinline__ void mixed_record(const EnsArgs &a, int i, double tp, MixedRec &r)
+{
+    if (PR == 3) {
+        predict_one_mixed(a, i, tp, r);
+        return;
+    }
+    Taylor p[3];
+    predict_one(a, i, tp, p);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float h = __double2float_rn(p[k].x);
+        r.xh[k] = h;
+        r.xl[k] = __double2float_rn(p[k].x - static_cast<double>(h));
+        r.v[k] = __double2float_rn(p[k].v);
+        r.a[k] = __double2float_rn(p[k].a);
+    }
+}
+
 template <int PR>
 __device__ void predict_slice(const EnsArgs &a, int lo, int hi, double tp)
 {
-    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
+    [[maybe_unused]] constexpr bool MIXED = PR == 1 || PR == 3, EXP = PR == 2;
     const size_t P = static_cast<size_t>(a.P);
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         if (MIXED) {
             MixedRec r;
-            predict_one_mixed(a, i, tp, r);
+            mixed_record<PR>(a, i, tp, r);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 a.jf32[k * P + i] = r.xh[k];
@@ -253,7 +289,7 @@ template <int PR>
 __device__ __forceinline__ void issue_ens_tile(const EnsArgs &a, unsigned char *smem, uint64_t *bar,
                                                int stage, int j0, int len)
 {
-    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
+    [[maybe_unused]] constexpr bool MIXED = PR == 1 || PR == 3, EXP = PR == 2;
     const int jt = a.jtile;
     const size_t P = static_cast<size_t>(a.P);
     if (MIXED || EXP) {
@@ -278,7 +314,7 @@ template <int PR>
 __device__ bool eval_share(const EnsArgs &a, int off, int nj, int s0, int s1, unsigned char *smem,
                            uint64_t *bar, unsigned &seq)
 {
-    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
+    [[maybe_unused]] constexpr bool MIXED = PR == 1 || PR == 3, EXP = PR == 2;
     const int T = blockDim.x, tid = threadIdx.x, jt = a.jtile;
     const int m = s1 - s0;
     if (m <= 0)
@@ -469,7 +505,7 @@ __device__ __forceinline__ float norm3f(float x, float y, float z)
     return m * sqrtf(fmaf(u, u, fmaf(v, v, w * w)));
 }
 
-// Mixed ensembles: the same corrector, interpolation and step with the
+// NB_MIXED32 ensembles: the same corrector, interpolation and step with the
 // arithmetic in FP32 (the forces carry FP32 pair rounding already, about
 // 1e-7 of each sum's condition number): the velocity and position
 // increments are formed in FP32 and added to the FP64 state, the crackle,
@@ -543,8 +579,8 @@ __device__ void correct_one_mixed(const EnsArgs &a, int i, double tn, const doub
 template <int PR>
 __device__ __forceinline__ void correct_particle(const EnsArgs &a, int i, double tn, const double (&f)[9])
 {
-    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
-    if (MIXED)
+    [[maybe_unused]] constexpr bool MIXED = PR == 1 || PR == 3, EXP = PR == 2;
+    if (PR == 3)
         correct_one_mixed(a, i, tn, f);
     else
         correct_one(a, i, tn, f);
@@ -554,7 +590,7 @@ __device__ __forceinline__ void correct_particle(const EnsArgs &a, int i, double
 template <int PR>
 __device__ void correct_share(const EnsArgs &a, int off, int s0, int s1, double tn)
 {
-    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
+    [[maybe_unused]] constexpr bool MIXED = PR == 1 || PR == 3, EXP = PR == 2;
     const size_t P = static_cast<size_t>(a.P);
     for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
         double f[9];
@@ -578,10 +614,10 @@ constexpr int kSmall = 16;
 template <int PR>
 __device__ __forceinline__ void store_ivalues(const EnsArgs &a, int i, double tn, double *iv)
 {
-    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
+    [[maybe_unused]] constexpr bool MIXED = PR == 1 || PR == 3, EXP = PR == 2;
     if (MIXED) {
         MixedRec r;
-        predict_one_mixed(a, i, tn, r);
+        mixed_record<PR>(a, i, tn, r);
         float *f = reinterpret_cast<float *>(iv);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -628,7 +664,7 @@ template <int PR>
 __device__ void eval_small(const EnsArgs &a, int lo, int hi, double tn, int K, const double (*iv)[9],
                            double (*part)[9], double (*wred)[9], unsigned char *smem, int cap)
 {
-    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
+    [[maybe_unused]] constexpr bool MIXED = PR == 1 || PR == 3, EXP = PR == 2;
     const int T = blockDim.x, tid = threadIdx.x;
     int K2 = 1;
     while (K2 < K)
@@ -680,7 +716,7 @@ __device__ void eval_small(const EnsArgs &a, int lo, int hi, double tn, int K, c
             const double mj = a.m[b + u];
             if (MIXED) {
                 MixedRec r;
-                predict_one_mixed(a, b + u, tn, r);
+                mixed_record<PR>(a, b + u, tn, r);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     sf[k * cap + u] = r.xh[k];
@@ -875,10 +911,38 @@ __device__ void init_share(const EnsArgs &a, int off, int s0, int s1, int pass)
     }
 }
 
+// Step log (nb_ensemble_set_log), written by rank 0 of the system's
+// cluster: the step's system, time and active count, and the active
+// particles' indices within the system (list[] holds ensemble indices).
+// Entries beyond the capacities are counted, not kept.
+__device__ void log_step(const EnsArgs &a, int c, double tn, int total, const int32_t *list, int off,
+                         long long *s_ip)
+{
+    if (threadIdx.x == 0) {
+        const unsigned long long e = atomicAdd(&a.log_cnt[0], 1ull);
+        const unsigned long long ip = atomicAdd(&a.log_cnt[1], static_cast<unsigned long long>(total));
+        const bool keep = ip + static_cast<unsigned long long>(total) <=
+                          static_cast<unsigned long long>(a.idx_cap);
+        if (e < static_cast<unsigned long long>(a.log_cap)) {
+            a.log_sys[e] = c;
+            a.log_t[e] = tn;
+            a.log_n[e] = total;
+            a.log_off[e] = keep ? static_cast<long long>(ip) : -1;
+        }
+        *s_ip = keep ? static_cast<long long>(ip) : -1;
+    }
+    __syncthreads();
+    const long long ip = *s_ip;
+    if (ip >= 0)
+        for (int k = threadIdx.x; k < total; k += blockDim.x)
+            a.log_idx[ip + k] = list[k] - off;
+    __syncthreads();
+}
+
 template <int PR>
 __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
 {
-    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
+    [[maybe_unused]] constexpr bool MIXED = PR == 1 || PR == 3, EXP = PR == 2;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ double red_d[32];
@@ -893,6 +957,7 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
     __shared__ double s_iv[kSmall][9];
     __shared__ double s_part[kSmall][9];
     __shared__ double s_wred[kEnsThreads / 32][9];
+    __shared__ long long s_log_ip;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = static_cast<int>(cl.block_rank());
     const int G = static_cast<int>(cl.num_blocks());
@@ -1004,6 +1069,8 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
                     store_ivalues<PR>(a, i, tn, s_iv[k]);
                 }
                 __syncthreads();
+                if (a.log_cnt && rank == 0)
+                    log_step(a, c, tn, total, s_act, off, &s_log_ip);
                 eval_small<PR>(a, lo, hi, tn, total, s_iv, s_part, s_wred, smem, 2 * a.jtile);
                 cl.sync();
                 for (int k = tid; k < total; k += T) {
@@ -1032,6 +1099,8 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
                 }
                 predict_slice<PR>(a, lo, hi, tn);
                 cl.sync();
+                if (a.log_cnt && rank == 0)
+                    log_step(a, c, tn, total, a.act + off, off, &s_log_ip);
                 const int q = (total + G - 1) / G;
                 const int s0 = min(total, rank * q), s1 = min(total, s0 + q);
                 const bool ok = eval_share<PR>(a, off, nj, s0, s1, smem, bar, seq);
@@ -1072,22 +1141,33 @@ nb_status ecuda(nb_ensemble *e, cudaError_t c, const char *where)
             return ecuda((e), e_, #call);           \
     } while (0)
 
-// Kernel instantiation of a precision: 0 FP64, 1 mixed, 2 EX.
+// Kernel instantiation of a precision: 0 FP64, 1 mixed, 2 EX, 3 mixed with
+// an FP32 state copy.
 int ens_kind(const nb_ensemble *e)
 {
-    return e->cfg.precision == NB_MIXED ? 1 : (e->cfg.precision == NB_EX ? 2 : 0);
+    switch (e->cfg.precision) {
+    case NB_MIXED: return 1;
+    case NB_EX: return 2;
+    case NB_MIXED32: return 3;
+    default: return 0;
+    }
+}
+
+bool ens_mixed(const nb_ensemble *e)
+{
+    return e->cfg.precision == NB_MIXED || e->cfg.precision == NB_MIXED32;
 }
 
 size_t ens_smem(const nb_ensemble *e)
 {
     const int k = ens_kind(e);
-    return static_cast<size_t>(2) * (k == 1 ? NCF * 4 : (k == 2 ? NCX * 4 : 5 * 16)) * e->jtile;
+    return static_cast<size_t>(2) * (k == 1 || k == 3 ? NCF * 4 : (k == 2 ? NCX * 4 : 5 * 16)) * e->jtile;
 }
 
 template <int PR>
 cudaError_t launch_ens(nb_ensemble *e, const EnsArgs &a, int grid_clusters)
 {
-    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
+    [[maybe_unused]] constexpr bool MIXED = PR == 1 || PR == 3, EXP = PR == 2;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid_clusters * e->G);
     cfg.blockDim = dim3(e->threads);
@@ -1106,7 +1186,7 @@ cudaError_t launch_ens(nb_ensemble *e, const EnsArgs &a, int grid_clusters)
 template <int PR>
 cudaError_t max_clusters(nb_ensemble *e, int *out)
 {
-    [[maybe_unused]] constexpr bool MIXED = PR == 1, EXP = PR == 2;
+    [[maybe_unused]] constexpr bool MIXED = PR == 1 || PR == 3, EXP = PR == 2;
     cudaError_t err = cudaFuncSetAttribute(ensemble_kernel<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(ens_smem(e)));
     if (err != cudaSuccess)
@@ -1135,7 +1215,7 @@ cudaError_t max_clusters(nb_ensemble *e, int *out)
 // 16 where the device co-schedules clusters of 16 blocks, else 8.
 int default_ctas(nb_ensemble *e)
 {
-    if (e->cfg.precision == NB_MIXED)
+    if (ens_mixed(e))
         return 4;
     const int keep = e->G;
     e->G = 16;
@@ -1149,7 +1229,20 @@ int default_ctas(nb_ensemble *e)
     return maxc >= 1 ? 16 : 8;
 }
 
-int default_jtile(const nb_ensemble *e) { return e->cfg.precision == NB_MIXED ? 1024 : 256; }
+int default_jtile(const nb_ensemble *e) { return ens_mixed(e) ? 1024 : 256; }
+
+template <int PR>
+cudaError_t max_clusters(nb_ensemble *e, int *out);
+
+cudaError_t max_clusters_kind(nb_ensemble *e, int *out)
+{
+    switch (ens_kind(e)) {
+    case 1: return max_clusters<1>(e, out);
+    case 2: return max_clusters<2>(e, out);
+    case 3: return max_clusters<3>(e, out);
+    default: return max_clusters<0>(e, out);
+    }
+}
 
 EnsArgs make_args(nb_ensemble *e, int mode, double t_end)
 {
@@ -1172,6 +1265,14 @@ EnsArgs make_args(nb_ensemble *e, int mode, double t_end)
     a.steps = e->steps;
     a.inter = e->inter;
     a.ctl = e->ctl;
+    a.log_cnt = e->log_cnt;
+    a.log_sys = e->log_sys;
+    a.log_n = e->log_n;
+    a.log_idx = e->log_idx;
+    a.log_t = e->log_t;
+    a.log_off = e->log_off;
+    a.log_cap = e->log_cap;
+    a.idx_cap = e->idx_cap;
     a.t_end = t_end;
     a.eps2 = e->eps * e->eps;
     a.eta = e->cfg.eta;
@@ -1189,13 +1290,20 @@ nb_status enqueue_run(nb_ensemble *e, int mode, double t_end)
 {
     int maxc = 0;
     const int kind = ens_kind(e);
-    ECU(e, kind == 1 ? max_clusters<1>(e, &maxc) : (kind == 2 ? max_clusters<2>(e, &maxc) : max_clusters<0>(e, &maxc)));
+    ECU(e, max_clusters_kind(e, &maxc));
     if (maxc < 1)
         return efail(e, NB_EINVAL, "ensemble launch shape does not fit on an SM");
     const int grid = std::min(maxc, e->nc);
     ECU(e, cudaMemsetAsync(e->queue, 0, sizeof(int), e->stream));
     const EnsArgs a = make_args(e, mode, t_end);
-    ECU(e, kind == 1 ? launch_ens<1>(e, a, grid) : (kind == 2 ? launch_ens<2>(e, a, grid) : launch_ens<0>(e, a, grid)));
+    cudaError_t le;
+    switch (kind) {
+    case 1: le = launch_ens<1>(e, a, grid); break;
+    case 2: le = launch_ens<2>(e, a, grid); break;
+    case 3: le = launch_ens<3>(e, a, grid); break;
+    default: le = launch_ens<0>(e, a, grid); break;
+    }
+    ECU(e, le);
     return NB_OK;
 }
 
@@ -1231,6 +1339,12 @@ void ens_free_all(nb_ensemble *e)
     cudaFree(e->jb64);
     cudaFree(e->jf32);
     cudaFree(e->st32);
+    cudaFree(e->log_cnt);
+    cudaFree(e->log_sys);
+    cudaFree(e->log_n);
+    cudaFree(e->log_idx);
+    cudaFree(e->log_t);
+    cudaFree(e->log_off);
     cudaFree(e->act);
     cudaFree(e->queue);
     cudaFree(e->steps);
@@ -1269,7 +1383,8 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
         nb_set_thread_error("n_systems >= 1 and non-NULL sizes, m, x, v are required");
         return NB_EINVAL;
     }
-    if ((cf.precision != NB_FP64 && cf.precision != NB_MIXED && cf.precision != NB_EX) || !(cf.eta > 0) ||
+    if ((cf.precision != NB_FP64 && cf.precision != NB_MIXED && cf.precision != NB_EX &&
+         cf.precision != NB_MIXED32) || !(cf.eta > 0) ||
         !(cf.eta_s > 0) ||
         !pow2(cf.dt_min) || !pow2(cf.dt_max) || cf.dt_min > cf.dt_max ||
         (cf.dt_shared != 0.0 && !pow2(cf.dt_shared))) {
@@ -1314,7 +1429,7 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
     // 1024; FP64 and EX 16 (or 8) x 128, j-tile 256 (set below, once the
     // device is known)
     e->jtile = default_jtile(e);
-    e->G = cf.precision == NB_MIXED ? 4 : 8;
+    e->G = ens_mixed(e) ? 4 : 8;
     auto bail = [&](nb_status s) {
         nb_set_thread_error(e->err.c_str());
         ens_free_all(e);
@@ -1361,11 +1476,13 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
     EI(cudaMalloc(&e->dt, P * sizeof(double)));
     EI(cudaMalloc(&e->anew, 9 * P * sizeof(double)));
     EI(cudaMalloc(&e->act, P * sizeof(int32_t)));
-    if (cf.precision == NB_MIXED) {
+    if (ens_mixed(e)) {
         EI(cudaMalloc(&e->jf32, 13 * P * sizeof(float)));
         EI(cudaMemsetAsync(e->jf32, 0, 13 * P * sizeof(float), e->stream));
-        EI(cudaMalloc(&e->st32, kSt32Rows * P * sizeof(float)));
-        EI(cudaMemsetAsync(e->st32, 0, kSt32Rows * P * sizeof(float), e->stream));
+        if (cf.precision == NB_MIXED32) {
+            EI(cudaMalloc(&e->st32, kSt32Rows * P * sizeof(float)));
+            EI(cudaMemsetAsync(e->st32, 0, kSt32Rows * P * sizeof(float), e->stream));
+        }
     } else if (cf.precision == NB_EX) {
         EI(cudaMalloc(&e->jf32, NCX * P * sizeof(float)));
         EI(cudaMemsetAsync(e->jf32, 0, NCX * P * sizeof(float), e->stream));
@@ -1484,8 +1601,7 @@ nb_status nb_ensemble_run(nb_ensemble *e, double t_end, int use_graph)
         }
         // occupancy query and attributes before capture
         int maxc = 0;
-        const int kind = ens_kind(e);
-        ECU(e, kind == 1 ? max_clusters<1>(e, &maxc) : (kind == 2 ? max_clusters<2>(e, &maxc) : max_clusters<0>(e, &maxc)));
+        ECU(e, max_clusters_kind(e, &maxc));
         ECU(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
         nb_status s = enqueue_run(e, 0, t_end);
         cudaGraph_t g = nullptr;
@@ -1565,6 +1681,88 @@ nb_status nb_ensemble_stats(nb_ensemble *e, int64_t *steps, double *interactions
         *interactions = static_cast<double>(it);
     if (launches)
         *launches = e->launches;
+    return NB_OK;
+}
+
+nb_status nb_ensemble_set_log(nb_ensemble *e, int64_t step_cap, int64_t idx_cap)
+{
+    if (!e)
+        return NB_EINVAL;
+    if (e->dead)
+        return NB_ECUDA;
+    if (step_cap < 0 || idx_cap < 0 || step_cap > (int64_t(1) << 32) || idx_cap > (int64_t(1) << 34))
+        return efail(e, NB_EINVAL, "step_cap in [0, 2^32] and idx_cap in [0, 2^34] required");
+    ECU(e, cudaStreamSynchronize(e->stream));
+    cudaFree(e->log_cnt);
+    cudaFree(e->log_sys);
+    cudaFree(e->log_n);
+    cudaFree(e->log_idx);
+    cudaFree(e->log_t);
+    cudaFree(e->log_off);
+    e->log_cnt = nullptr;
+    e->log_sys = e->log_n = e->log_idx = nullptr;
+    e->log_t = nullptr;
+    e->log_off = nullptr;
+    e->log_cap = e->idx_cap = 0;
+    // the launch arguments (captured in the graph) change
+    if (e->exec) {
+        cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
+    }
+    if (e->graph) {
+        cudaGraphDestroy(e->graph);
+        e->graph = nullptr;
+    }
+    e->graph_t_end = -1.0;
+    if (step_cap == 0 && idx_cap == 0)
+        return NB_OK;
+    const size_t sc = static_cast<size_t>(std::max<int64_t>(1, step_cap));
+    const size_t ic = static_cast<size_t>(std::max<int64_t>(1, idx_cap));
+    cudaError_t c = cudaMalloc(&e->log_cnt, 2 * sizeof(unsigned long long));
+    if (c == cudaSuccess) c = cudaMalloc(&e->log_sys, sc * sizeof(int32_t));
+    if (c == cudaSuccess) c = cudaMalloc(&e->log_n, sc * sizeof(int32_t));
+    if (c == cudaSuccess) c = cudaMalloc(&e->log_t, sc * sizeof(double));
+    if (c == cudaSuccess) c = cudaMalloc(&e->log_off, sc * sizeof(int64_t));
+    if (c == cudaSuccess) c = cudaMalloc(&e->log_idx, ic * sizeof(int32_t));
+    if (c == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        nb_ensemble_set_log(e, 0, 0);
+        return efail(e, NB_ENOMEM, "no device memory for the step log");
+    }
+    ECU(e, c);
+    ECU(e, cudaMemsetAsync(e->log_cnt, 0, 2 * sizeof(unsigned long long), e->stream));
+    e->log_cap = step_cap;
+    e->idx_cap = idx_cap;
+    return NB_OK;
+}
+
+nb_status nb_ensemble_get_log(nb_ensemble *e, int32_t *sys, double *t, int32_t *n_act, int64_t *idx_off,
+                              int32_t *idx, int64_t *n_steps, int64_t *n_idx)
+{
+    if (!e)
+        return NB_EINVAL;
+    if (e->dead)
+        return NB_ECUDA;
+    unsigned long long cnt[2] = {0, 0};
+    if (e->log_cnt)
+        ECU(e, cudaMemcpyAsync(cnt, e->log_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, e->stream));
+    ECU(e, cudaStreamSynchronize(e->stream));
+    const size_t ks = static_cast<size_t>(std::min<unsigned long long>(cnt[0], e->log_cap));
+    const size_t ki = static_cast<size_t>(std::min<unsigned long long>(cnt[1], e->idx_cap));
+    if (ks > 0) {
+        if (sys) ECU(e, cudaMemcpyAsync(sys, e->log_sys, ks * sizeof(int32_t), cudaMemcpyDeviceToHost, e->stream));
+        if (t) ECU(e, cudaMemcpyAsync(t, e->log_t, ks * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
+        if (n_act) ECU(e, cudaMemcpyAsync(n_act, e->log_n, ks * sizeof(int32_t), cudaMemcpyDeviceToHost, e->stream));
+        if (idx_off)
+            ECU(e, cudaMemcpyAsync(idx_off, e->log_off, ks * sizeof(int64_t), cudaMemcpyDeviceToHost, e->stream));
+    }
+    if (ki > 0 && idx)
+        ECU(e, cudaMemcpyAsync(idx, e->log_idx, ki * sizeof(int32_t), cudaMemcpyDeviceToHost, e->stream));
+    ECU(e, cudaStreamSynchronize(e->stream));
+    if (n_steps)
+        *n_steps = static_cast<int64_t>(cnt[0]);
+    if (n_idx)
+        *n_idx = static_cast<int64_t>(cnt[1]);
     return NB_OK;
 }
 

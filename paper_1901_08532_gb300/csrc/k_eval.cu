@@ -33,7 +33,8 @@ __host__ __device__ constexpr int max_threads_for(int ki) { return ki == 1 ? 512
 
 struct EvalArgs {
     const void *jb;      // [NC][n] 16-byte records
-    int n;               // j count (= record stride)
+    int n;               // record stride (j count of the buffer)
+    int j0, j1;          // j-range evaluated, [j0, j1) (the whole buffer: 0, n)
     const int32_t *act;  // [n_act]
     int n_act;
     double *out;         // [9][ostride]
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs
         const int p = ibase + slot + k * slots;
         kidx[k] = p < a.n_act ? p : -1;
         const int i = a.act[p < a.n_act ? p : a.n_act - 1];
-        const double2 r0 = jb[i], r1 = jb[a.n + i], r2 = jb[2 * (size_t)a.n + i];
+        const double2 r0 = jb[i], r1 = jb[(size_t)a.n + i], r2 = jb[2 * (size_t)a.n + i];
         const double2 r3 = jb[3 * (size_t)a.n + i], r4 = jb[4 * (size_t)a.n + i];
         xi[k] = r0.x; yi[k] = r0.y; zi[k] = r1.x;
         vxi[k] = r2.x; vyi[k] = r2.y; vzi[k] = r3.x;
@@ -148,8 +149,8 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs
             acc[q][k] = 0.0;
     }
 
-    const int jbeg = blockIdx.y * a.jchunk;
-    const int jend = min(a.n, jbeg + a.jchunk);
+    const int jbeg = a.j0 + blockIdx.y * a.jchunk;
+    const int jend = min(a.j1, jbeg + a.jchunk);
     const int ntiles = jend > jbeg ? (jend - jbeg + jt - 1) / jt : 0;
     int issued = 0;
     if (tid == 0) {
@@ -249,21 +250,29 @@ __device__ __forceinline__ void issue_tile_rows(unsigned char *smem, uint64_t *b
 }
 
 // Block-size limit and minimum resident blocks of the mixed kernel: KI = 2
-// runs 3 blocks of 128 threads per SM (12 warps, <= 170 registers), KI = 1
-// 2 blocks of 256.  The compensated (hi, lo) accumulators, touched once per
-// tile, live in shared memory after the tiles: rows [18 * KI][threads].
+// runs 3 blocks of 128 threads per SM (12 warps, <= 170 registers), KI = 3
+// 2 blocks of 128 (<= 255 registers), KI = 1 2 blocks of 256.  The
+// compensated (hi, lo) accumulators, touched once per tile, live in shared
+// memory after the tiles: rows [18 * KI][threads].
 __host__ __device__ constexpr int mixed_max_threads(int ki) { return ki == 1 ? 256 : 128; }
-__host__ __device__ constexpr int mixed_min_blocks(int ki) { return ki == 1 ? 2 : 3; }
+__host__ __device__ constexpr int mixed_min_blocks(int ki) { return ki == 2 ? 3 : 2; }
 
 // JU j-particles per inner iteration (2: one pair, 4: two pairs from one
-// 128-bit load per row).
-template <int KI, int JU>
+// 128-bit load per row).  JT > 0 fixes the j-tile length at compile time
+// (the launch's jtile must equal it), so that every shared-memory row of the
+// inner loop is addressed by a constant offset from one base; JT = 0 takes
+// it from the launch.  More i-particles per thread (KI) give each warp more
+// independent pair terms, which the packed FMAs need: each reads three
+// 64-bit register operands, and the register file sustains that for only
+// about two thirds of the pipe's rate (k_peaks.cu, kind 8).
+template <int KI, int JU, int JT>
 __global__ void __launch_bounds__(mixed_max_threads(KI), mixed_min_blocks(KI))
     eval_mixed_kernel(EvalArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
-    const int tid = threadIdx.x, lanes = a.lanes, jt = a.jtile;
+    const int tid = threadIdx.x, lanes = a.lanes;
+    const int jt = JT > 0 ? JT : a.jtile;
     const int slot = tid / lanes, lj = tid - slot * lanes;
     const int slots = blockDim.x / lanes;
     const int ibase = blockIdx.x * slots * KI;
@@ -290,8 +299,8 @@ __global__ void __launch_bounds__(mixed_max_threads(KI), mixed_min_blocks(KI))
             acc_s[(q * KI + k) * nthr + tid] = 0.0f;
     }
 
-    const int jbeg = blockIdx.y * a.jchunk;
-    const int jend = min(a.n, jbeg + a.jchunk);
+    const int jbeg = a.j0 + blockIdx.y * a.jchunk;
+    const int jend = min(a.j1, jbeg + a.jchunk);
     const int ntiles = jend > jbeg ? (jend - jbeg + jt - 1) / jt : 0;
     int issued = 0;
     if (tid == 0) {
@@ -438,8 +447,8 @@ __global__ void __launch_bounds__(kExThreads, 2) eval_ex_kernel(EvalArgs a)
     for (int q = 0; q < 9; ++q)
         acc[q][0] = 0.0;
 
-    const int jbeg = blockIdx.y * a.jchunk;
-    const int jend = min(a.n, jbeg + a.jchunk);
+    const int jbeg = a.j0 + blockIdx.y * a.jchunk;
+    const int jend = min(a.j1, jbeg + a.jchunk);
     const int ntiles = jend > jbeg ? (jend - jbeg + jt - 1) / jt : 0;
     int issued = 0;
     if (tid == 0) {
@@ -499,6 +508,26 @@ constexpr int kRecBytes64 = 5 * 16;
 constexpr int kRecBytes32 = NCF * 4;
 constexpr int kRecBytesEx = NCX * 4;
 
+using EvalKernel = void (*)(EvalArgs);
+
+// The mixed kernel for KI i-particles per thread, JU j per inner iteration
+// and j-tile jt (compile-time where an instantiation exists); nullptr for a
+// combination that is not built (KI = 3 runs with JU = 4 only).
+EvalKernel mixed_kernel(int ki, int ju, int jt)
+{
+    if (ki == 1)
+        return ju == 2 ? eval_mixed_kernel<1, 2, 0> : eval_mixed_kernel<1, 4, 0>;
+    if (ki == 2 && ju == 2)
+        return eval_mixed_kernel<2, 2, 0>;
+    if (ki == 2)
+        return jt == 512 ? eval_mixed_kernel<2, 4, 512> : jt == 256 ? eval_mixed_kernel<2, 4, 256>
+                                                                    : eval_mixed_kernel<2, 4, 0>;
+    if (ki == 3 && ju == 4)
+        return jt == 512 ? eval_mixed_kernel<3, 4, 512> : jt == 256 ? eval_mixed_kernel<3, 4, 256>
+                                                                    : eval_mixed_kernel<3, 4, 0>;
+    return nullptr;
+}
+
 template <typename K>
 cudaError_t set_smem_attr(K kernel)
 {
@@ -515,12 +544,14 @@ cudaError_t nb_eval_smem_setup()
     if ((e = set_smem_attr(eval_fp64_kernel<1>)) != cudaSuccess) return e;
     if ((e = set_smem_attr(eval_fp64_kernel<2>)) != cudaSuccess) return e;
     if ((e = set_smem_attr(eval_fp64_kernel<4>)) != cudaSuccess) return e;
-    if ((e = set_smem_attr(eval_mixed_kernel<1, 2>)) != cudaSuccess) return e;
-    if ((e = set_smem_attr(eval_mixed_kernel<1, 4>)) != cudaSuccess) return e;
-    if ((e = set_smem_attr(eval_mixed_kernel<2, 2>)) != cudaSuccess) return e;
+    for (int ki = 1; ki <= 3; ++ki)
+        for (int ju = 2; ju <= 4; ju += 2)
+            for (int jt = 0; jt <= 512; jt += 256)
+                if (const EvalKernel k = mixed_kernel(ki, ju, jt))
+                    if ((e = set_smem_attr(k)) != cudaSuccess) return e;
     if ((e = set_smem_attr(eval_ex_kernel<float>)) != cudaSuccess) return e;
     if ((e = set_smem_attr(eval_ex_kernel<float2>)) != cudaSuccess) return e;
-    return set_smem_attr(eval_mixed_kernel<2, 4>);
+    return cudaSuccess;
 }
 
 // Blocks of the chosen evaluation kernel that fit on one SM.
@@ -536,10 +567,8 @@ int resident_blocks(const nb_ctx *c, const nb_tiles &t)
         if (t.junroll == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_ex_kernel<float>, t.threads, smem);
         else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_ex_kernel<float2>, t.threads, smem);
     } else if (mixed) {
-        if (t.ki == 1 && t.junroll == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_mixed_kernel<1, 2>, t.threads, smem);
-        else if (t.ki == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_mixed_kernel<1, 4>, t.threads, smem);
-        else if (t.junroll == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_mixed_kernel<2, 2>, t.threads, smem);
-        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_mixed_kernel<2, 4>, t.threads, smem);
+        const EvalKernel k = mixed_kernel(t.ki, t.junroll, t.jtile);
+        e = k ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, t.threads, smem) : cudaErrorInvalidValue;
     } else {
         if (t.ki == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_fp64_kernel<1>, t.threads, smem);
         else if (t.ki == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_fp64_kernel<2>, t.threads, smem);
@@ -556,7 +585,7 @@ int resident_blocks(const nb_ctx *c, const nb_tiles &t)
 // split.  Small ones: lanes share an i so that a block's i-slots are not
 // mostly empty, and the j-range is split across blocks until the grid
 // covers every SM several times.
-nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req)
+nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req, int64_t j_count)
 {
     nb_tiles t = req;
     const bool ex = c->cfg.precision == NB_EX;
@@ -566,7 +595,7 @@ nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req)
     // active set fills the grid without splitting
     const bool big = n_act >= 16384;
     if (t.ki <= 0)
-        t.ki = mixed ? 2 : 1;
+        t.ki = mixed ? (big ? 3 : 2) : 1;
     if (t.threads <= 0)
         t.threads = ex ? kExThreads : mixed ? mixed_max_threads(t.ki) : 128;
     if (t.junroll <= 0)
@@ -585,7 +614,7 @@ nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req)
         // Split the j-range so that the grid fills whole waves of resident
         // blocks: all blocks of a launch do equal work, so a partial last
         // wave idles the rest of the GPU for a whole block's duration.
-        const int64_t jn = (mixed || ex) ? c->npad : c->n;
+        const int64_t jn = j_count > 0 ? j_count : ((mixed || ex) ? c->npad : c->n);
         const int64_t itile = static_cast<int64_t>(t.threads / t.lanes) * t.ki;
         const int64_t nblk = (n_act + itile - 1) / itile;
         const int64_t cap = static_cast<int64_t>(c->sm_count) * resident_blocks(c, t);
@@ -619,7 +648,8 @@ cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L)
         return cudaSuccess;
     const bool mixed = nb_fp32_eval(c->cfg.precision);
     const bool ex = c->cfg.precision == NB_EX;
-    if (!(t.ki == 1 || (t.ki == 2 && !ex) || (t.ki == 4 && !mixed && !ex)) || t.threads < 32 ||
+    if (!(t.ki == 1 || (t.ki == 2 && !ex) || (t.ki == 3 && mixed && t.junroll == 4) ||
+          (t.ki == 4 && !mixed && !ex)) || t.threads < 32 ||
         t.threads > (ex ? kExThreads : mixed ? mixed_max_threads(t.ki) : max_threads_for(t.ki)) ||
         t.threads % 32 || !is_pow2(t.lanes) || t.lanes > 32 || t.jtile < 1 || t.split < 1)
         return cudaErrorInvalidValue;
@@ -634,15 +664,22 @@ cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L)
         return cudaErrorInvalidValue;
     const int itile = (t.threads / t.lanes) * t.ki;
     const int gx = (L.n_act + itile - 1) / itile;
-    // j chunk per split, a whole number of tiles
-    const int64_t jn = (mixed || ex) ? c->npad : c->n;
-    int64_t chunk = (jn + t.split - 1) / t.split;
+    // j-range (the whole buffer unless L.j1 >= 0) and chunk per split, a
+    // whole number of tiles
+    const int64_t nbuf = (mixed || ex) ? c->npad : c->n;
+    const int64_t j0 = L.j1 >= 0 ? L.j0 : 0, j1 = L.j1 >= 0 ? L.j1 : nbuf;
+    if (j0 < 0 || j1 > nbuf || j0 > j1 || ((mixed || ex) && (j0 % 4 || j1 % 4)))
+        return cudaErrorInvalidValue;
+    const int64_t jn = j1 - j0;
+    int64_t chunk = std::max<int64_t>(1, (jn + t.split - 1) / t.split);
     chunk = (chunk + t.jtile - 1) / t.jtile * t.jtile;
-    const int split = static_cast<int>((jn + chunk - 1) / chunk);
+    const int split = std::max(1, static_cast<int>((jn + chunk - 1) / chunk));
 
     EvalArgs a;
     a.jb = (mixed || ex) ? static_cast<const void *>(c->jf32) : static_cast<const void *>(c->jb64);
-    a.n = static_cast<int>(jn);
+    a.n = static_cast<int>(nbuf);
+    a.j0 = static_cast<int>(j0);
+    a.j1 = static_cast<int>(j1);
     a.act = L.act;
     a.n_act = L.n_act;
     a.out = L.out;
@@ -688,17 +725,15 @@ cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L)
         if (t.junroll == 1) eval_ex_kernel<float><<<grid, block, smem, c->stream>>>(a);
         else eval_ex_kernel<float2><<<grid, block, smem, c->stream>>>(a);
     } else if (mixed) {
-        if (t.ki == 1 && t.junroll == 2) eval_mixed_kernel<1, 2><<<grid, block, smem, c->stream>>>(a);
-        else if (t.ki == 1) eval_mixed_kernel<1, 4><<<grid, block, smem, c->stream>>>(a);
-        else if (t.junroll == 2) eval_mixed_kernel<2, 2><<<grid, block, smem, c->stream>>>(a);
-        else eval_mixed_kernel<2, 4><<<grid, block, smem, c->stream>>>(a);
+        mixed_kernel(t.ki, t.junroll, t.jtile)<<<grid, block, smem, c->stream>>>(a);
     } else {
         if (t.ki == 1) eval_fp64_kernel<1><<<grid, block, smem, c->stream>>>(a);
         else if (t.ki == 2) eval_fp64_kernel<2><<<grid, block, smem, c->stream>>>(a);
         else eval_fp64_kernel<4><<<grid, block, smem, c->stream>>>(a);
     }
     c->launches += 1;
-    c->interactions += static_cast<double>(L.n_act) * static_cast<double>(c->n);
+    c->interactions += static_cast<double>(L.n_act) *
+                       static_cast<double>(L.j1 >= 0 ? std::min<int64_t>(j1, c->n) - j0 : c->n);
     return cudaGetLastError();
 }
 
@@ -719,6 +754,8 @@ cudaError_t nb_launch_eval_fp64_rows(const double2 *rec, int n, const int32_t *a
     EvalArgs a;
     a.jb = rec;
     a.n = n;
+    a.j0 = 0;
+    a.j1 = n;
     a.act = act;
     a.n_act = n;
     a.out = out;
@@ -792,13 +829,45 @@ extern "C" nb_status nb_evaluate_fp64_static(const void *jrec, int64_t n, const 
                                              int64_t n_act, double eps, int32_t split, double *out,
                                              void *stream)
 {
+    // every argument check comes before the first CUDA call, so a rejected
+    // call never launches or queues anything
     if (!jrec || !active || !out || n < 1 || n > 0x7fffffffLL || n_act < 0 || n_act > n ||
         split < 0 || !(eps >= 0x1p-60) || !(eps <= 1e18)) {
         nb_set_thread_error("nb_evaluate_fp64_static: invalid argument");
         return NB_EINVAL;
     }
+    if ((reinterpret_cast<uintptr_t>(jrec) & 15) || (reinterpret_cast<uintptr_t>(active) & 3) ||
+        (reinterpret_cast<uintptr_t>(out) & 7)) {
+        nb_set_thread_error("nb_evaluate_fp64_static: jrec must be 16-byte, active 4-byte and out "
+                            "8-byte aligned");
+        return NB_EINVAL;
+    }
     if (n_act == 0)
         return NB_OK;
+
+    // launch shape: one i per thread slot, lanes share an i for small sets
+    const int threads = 128, jt = 128;
+    int lanes = 1;
+    while (lanes < 32 && static_cast<int64_t>(threads / (2 * lanes)) >= n_act)
+        lanes *= 2;
+    const int itile = threads / lanes;
+    const int64_t gx = (n_act + itile - 1) / itile;
+    const size_t part_per_split = static_cast<size_t>(9) * n_act;
+    if (split > 1) {
+        int64_t chunk = (n + split - 1) / split;
+        chunk = (chunk + jt - 1) / jt * jt;
+        const int64_t splits = (n + chunk - 1) / chunk;
+        if (splits > 65535) {
+            nb_set_thread_error("nb_evaluate_fp64_static: split gives more than 65535 j-chunks");
+            return NB_EINVAL;
+        }
+        if (static_cast<size_t>(splits) * part_per_split > kStaticPartDoubles || gx > kStaticMaxTiles) {
+            nb_set_thread_error("nb_evaluate_fp64_static: split * 9 * n_act doubles exceed the "
+                                "16 MiB static scratch");
+            return NB_EINVAL;
+        }
+    }
+
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
@@ -816,28 +885,16 @@ extern "C" nb_status nb_evaluate_fp64_static(const void *jrec, int64_t n, const 
         return NB_ECUDA;
     }
 
-    // launch shape: one i per thread slot, lanes share an i for small sets
-    const int threads = 128, jt = 128;
-    int lanes = 1;
-    while (lanes < 32 && static_cast<int64_t>(threads / (2 * lanes)) >= n_act)
-        lanes *= 2;
-    const int itile = threads / lanes;
-    const int64_t gx = (n_act + itile - 1) / itile;
-    const size_t part_per_split = static_cast<size_t>(9) * n_act;
     int64_t s = split;
     if (s == 0) {
+        // enough blocks to cover every SM four times, within the scratch
         const int64_t target = static_cast<int64_t>(sms) * 4;
         s = gx >= target ? 1 : (target + gx - 1) / gx;
         s = std::min<int64_t>(s, std::max<int64_t>(1, n / (2 * jt)));
         s = std::min<int64_t>(s, static_cast<int64_t>(kStaticPartDoubles / part_per_split));
         if (gx > kStaticMaxTiles)
             s = 1;
-        s = std::max<int64_t>(1, s);
-    } else if (s > 1 && (static_cast<size_t>(s) * part_per_split > kStaticPartDoubles ||
-                         gx > kStaticMaxTiles)) {
-        nb_set_thread_error("nb_evaluate_fp64_static: split * 9 * n_act doubles exceed the "
-                            "16 MiB static scratch");
-        return NB_EINVAL;
+        s = std::max<int64_t>(1, std::min<int64_t>(s, 65535));
     }
     int64_t chunk = (n + s - 1) / s;
     chunk = (chunk + jt - 1) / jt * jt;
@@ -854,6 +911,8 @@ extern "C" nb_status nb_evaluate_fp64_static(const void *jrec, int64_t n, const 
     EvalArgs a;
     a.jb = jrec;
     a.n = static_cast<int>(n);
+    a.j0 = 0;
+    a.j1 = static_cast<int>(n);
     a.act = active;
     a.n_act = static_cast<int>(n_act);
     a.out = out;

@@ -78,8 +78,8 @@ std::string check_config(const nb_config &c)
 
 std::string check_tiles(const nb_tiles &t)
 {
-    if (t.ki != 0 && t.ki != 1 && t.ki != 2 && t.ki != 4)
-        return "tiles.ki must be 0, 1, 2 or 4";
+    if (t.ki < 0 || t.ki > 4)
+        return "tiles.ki must be 0, 1, 2, 3 or 4";
     if (t.threads != 0 && (t.threads < 32 || t.threads > 512 || t.threads % 32))
         return "tiles.threads must be 0 or a multiple of 32 in [32, 512]";
     if (t.lanes != 0 && (t.lanes > 32 || (t.lanes & (t.lanes - 1))))
@@ -547,6 +547,110 @@ nb_status nb_evaluate(nb_ctx *c, const int32_t *active, int64_t n_act, int activ
     }
     if (host_copy)
         return sync_ctl(c);
+    return NB_OK;
+}
+
+nb_status nb_schedule(nb_ctx *c, double *t_next, int64_t *n_act)
+{
+    CHECK_CTX(c);
+    double tn;
+    int64_t na;
+    nb_status s = schedule(c, &tn, &na);
+    if (s != NB_OK)
+        return s;
+    std::swap(c->act, c->act_next);
+    c->n_act = na;
+    c->have_eval = false;
+    if (t_next)
+        *t_next = tn;
+    if (n_act)
+        *n_act = na;
+    return NB_OK;
+}
+
+// Copy an active list into c->act (checked when it is a host list).
+nb_status load_active(nb_ctx *c, const int32_t *active, int64_t n_act, int active_on_device)
+{
+    if (n_act < 0 || n_act > c->n)
+        return fail(c, NB_EINVAL, "n_act must be in [0, n]");
+    if (!active && n_act != c->n)
+        return fail(c, NB_EINVAL, "active == NULL requires n_act == n");
+    if (active && !active_on_device)
+        for (int64_t k = 0; k < n_act; ++k)
+            if (active[k] < 0 || active[k] >= c->n)
+                return fail(c, NB_EINVAL, "active index out of range");
+    if (n_act == 0)
+        return NB_OK;
+    if (!active)
+        CU(c, nb_launch_iota(c, static_cast<int>(c->n), c->act));
+    else if (active != c->act)
+        CU(c, cudaMemcpyAsync(c->act, active, static_cast<size_t>(n_act) * sizeof(int32_t),
+                              active_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->stream));
+    return NB_OK;
+}
+
+nb_status nb_evaluate_partial(nb_ctx *c, const int32_t *active, int64_t n_act, int active_on_device,
+                              int64_t j_lo, int64_t j_hi, double *part, int part_on_device)
+{
+    CHECK_CTX(c);
+    if (!c->have_pred)
+        return fail(c, NB_ESTATE, "nb_evaluate_partial needs a prediction (nb_predict) first");
+    if (!part)
+        return fail(c, NB_EINVAL, "part must not be NULL");
+    const bool rows = nb_jrows(c->cfg.precision) > 0;
+    if (j_lo < 0 || j_hi > c->n || j_lo > j_hi)
+        return fail(c, NB_EINVAL, "j-range must satisfy 0 <= j_lo <= j_hi <= n");
+    if (rows && (j_lo % 4 || (j_hi % 4 && j_hi != c->n)))
+        return fail(c, NB_EINVAL, "FP32-row precisions need j_lo and j_hi multiples of 4 (or j_hi == n)");
+    nb_status s = load_active(c, active, n_act, active_on_device);
+    if (s != NB_OK)
+        return s;
+    // the partial sums overwrite the context's evaluation results
+    c->have_eval = false;
+    if (n_act == 0)
+        return NB_OK;
+    EvalLaunch L;
+    L.act = c->act;
+    L.n_act = static_cast<int>(n_act);
+    L.ostride = static_cast<int>(n_act);
+    L.out = part_on_device ? part : c->anew;
+    L.j0 = j_lo;
+    L.j1 = rows && j_hi == c->n ? c->npad : j_hi;
+    L.tiles = nb_auto_tiles(c, n_act, c->cfg.tiles, L.j1 - L.j0);
+    cudaError_t e = nb_launch_eval(c, L);
+    if (e == cudaErrorInvalidValue)
+        return fail(c, NB_EINVAL, "evaluation launch shape is not valid for this size");
+    CU(c, e);
+    if (!part_on_device) {
+        CU(c, cudaMemcpyAsync(part, c->anew, static_cast<size_t>(9 * n_act) * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+        return sync_ctl(c);
+    }
+    return NB_OK;
+}
+
+nb_status nb_set_forces(nb_ctx *c, const int32_t *active, int64_t n_act, int active_on_device,
+                        const double *f, int f_on_device)
+{
+    CHECK_CTX(c);
+    if (!c->have_pred)
+        return fail(c, NB_ESTATE, "nb_set_forces needs a prediction (nb_predict) first");
+    if (!f && n_act > 0)
+        return fail(c, NB_EINVAL, "f must not be NULL");
+    if (f && !f_on_device && !finite_all(f, 9 * n_act))
+        return fail(c, NB_ENONFINITE, "forces must be finite");
+    nb_status s = load_active(c, active, n_act, active_on_device);
+    if (s != NB_OK)
+        return s;
+    if (n_act > 0)
+        CU(c, cudaMemcpy2DAsync(c->anew, static_cast<size_t>(c->n) * sizeof(double), f,
+                                static_cast<size_t>(n_act) * sizeof(double),
+                                static_cast<size_t>(n_act) * sizeof(double), 9,
+                                f_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    c->n_act = n_act;
+    c->have_eval = true;
+    c->t_eval = c->t_pred;
     return NB_OK;
 }
 

@@ -180,7 +180,7 @@ constexpr int NCX = 20;
 __device__ __forceinline__ float rsqrt_est_v(float x)
 {
     float y;
-    asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 __device__ __forceinline__ float2 rsqrt_est_v(float2 x) { return make_float2(rsqrt_est_v(x.x), rsqrt_est_v(x.y)); }

@@ -181,7 +181,7 @@ __device__ __forceinline__ double rsqrt_fp64(double x)
     // double (11-bit exponent, bias 1023) -> float (8-bit, bias 127), mantissa truncated
     const unsigned fb = (static_cast<unsigned>(hi - (896 << 20)) << 3) | (lo >> 29);
     float yf;
-    asm("rsqrt.approx.f32 %0, %1;" : "=f"(yf) : "f"(__uint_as_float(fb)));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__uint_as_float(fb)));
     const unsigned yb = __float_as_uint(yf);
     const double y0 = __hiloint2double(static_cast<int>((yb >> 3) + (896u << 20)),
                                        static_cast<int>(yb << 29));
@@ -211,11 +211,13 @@ struct EvalLaunch {
     double *out;         // [9][ostride]
     int ostride;
     nb_tiles tiles;      // resolved
+    int64_t j0 = 0, j1 = -1;  // j-range [j0, j1) of the evaluation buffer; j1 < 0: all of it
 };
 
 // k_eval.cu
 cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L);
-nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req);
+// j_count: length of the j-range evaluated (0: the whole buffer)
+nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req, int64_t j_count = 0);
 cudaError_t nb_eval_smem_setup();
 // k_predict.cu
 cudaError_t nb_launch_predict(nb_ctx *c, double t);

@@ -104,3 +104,23 @@ def test_ensemble_rejects_single_precision_and_bad_sizes():
                               m.ctypes.data_as(d), x.ctypes.data_as(d), v.ctypes.data_as(d), 1e-3,
                               C.byref(_cfg()))
     assert st == nb.NB_EINVAL and not e.value
+
+
+@pytest.mark.parametrize("jrec, act, out, n, n_act, split, msg", [
+    (0x1008, 0x2000, 0x3000, 1000, 10, 0, b"aligned"),     # jrec only 8-byte aligned
+    (0x1000, 0x2002, 0x3000, 1000, 10, 0, b"aligned"),     # active not 4-byte aligned
+    (0x1000, 0x2000, 0x3004, 1000, 10, 0, b"aligned"),     # out not 8-byte aligned
+    (0x1000, 0x2000, 0x3000, 1 << 24, 1, 200000, b"65535"),  # too many j-chunks
+    (0x1000, 0x2000, 0x3000, 1 << 16, 1 << 14, 64, b"static scratch"),  # partials too large
+    (0x1000, 0x2000, 0x3000, 1 << 20, 600000, 2, b"static scratch"),    # more than 4096 i-tiles
+    (0x1000, 0x2000, 0x3000, 1000, 1001, 0, b"invalid argument"),       # n_act > n
+])
+def test_static_entry_rejects_before_any_cuda_call(jrec, act, out, n, n_act, split, msg):
+    """The allocation-free entry point checks pointers' alignment and the
+    explicit split on the host and returns NB_EINVAL without launching: the
+    pointers here are not device memory, and no GPU is needed."""
+    lib.nb_evaluate_fp64_static.restype = C.c_int
+    st = lib.nb_evaluate_fp64_static(C.c_void_p(jrec), n, C.c_void_p(act), n_act, 1e-3, split,
+                                     C.c_void_p(out), None)
+    assert st == nb.NB_EINVAL
+    assert msg in lib.nb_last_error(None)

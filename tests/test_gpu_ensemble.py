@@ -5,7 +5,7 @@ import pytest
 
 import nb_inputs as ni
 import oracle as O
-from nbhelp import nb_gpu, rel_err
+from nbhelp import check_parity, nb_gpu, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -68,13 +68,71 @@ def test_fp64_ensemble_launch_shapes_agree():
         np.testing.assert_array_equal(st["t"], out[0]["t"])
 
 
+@pytest.mark.parametrize("prec, tol_xv", [(1, 1e-9), (4, 1e-7)])
+def test_mixed_ensembles_match_oracle_replay_per_system(prec, tol_xv):
+    """Mixed ensembles against the FP64 oracle, system by system.  FP32 pair
+    arithmetic may move a step decision across a power of two (another valid
+    trajectory), so the oracle replays each system's logged (t_next, active
+    set) sequence from the ensemble's own starting state; then t must agree
+    exactly, x and v per particle to tol_xv of |x|, |v|, and a, jerk and
+    snap to 1e-6 of each sum's condition number sum_j |T_ij| plus twice the
+    change the oracle's own sums show between the two final states (the
+    inputs differ: positions by the accumulated force rounding, and the
+    snap's a_j - a_i by the mixed accelerations of the previous steps).
+    Every particle is evaluated at t_end in the last step.  NB_MIXED (1)
+    predicts and corrects in FP64: 1e-9.  NB_MIXED32 (4) forms the
+    corrector's increments in FP32 (about 6e-8 of each increment): 1e-7.
+    The run is short (to t = 2^-10, block steps down to 2^-20), since the
+    per-step force rounding of a few 1e-8 grows along close encounters."""
+    nb = nb_gpu()
+    sizes = [2, 5, 16, 33, 300, 64, 257]
+    ms, xs, vs = _systems(sizes, 110)
+    eps, t_end = 1e-4, 2.0 ** -10
+    ens = nb.Ensemble(sizes, *_concat(ms, xs, vs), eps, precision=prec, dt_max=t_end)
+    st0 = ens.state()
+    ens.set_log(1 << 20, 1 << 24)
+    ens.run(t_end)
+    st = ens.state()
+    steps, _, _ = ens.stats()
+    log, (n_steps, n_idx) = ens.log()
+    ens.close()
+    assert n_steps == int(steps.sum()) and n_steps <= 1 << 20 and n_idx <= 1 << 24
+    small = large = 0
+    o = 0
+    for k, n in enumerate(sizes):
+        sl = slice(o, o + n)
+        o += n
+        tn = [t for t, _ in log[k]]
+        sets = [idx for _, idx in log[k]]
+        assert len(tn) == steps[k] and all(q is not None for q in sets)
+        assert all(np.all(np.diff(q) > 0) for q in sets) and tn == sorted(tn)
+        small += sum(len(q) <= 16 for q in sets)
+        large += sum(len(q) > 16 for q in sets)
+        ref = O.System(ms[k], xs[k], vs[k], eps, dt_max=t_end)
+        ref.set_state({f: st0[f][sl] for f in ("x", "v", "a", "j", "s", "c", "t", "dt")})
+        ref.replay(tn, sets)
+        sr = ref.state()
+        np.testing.assert_array_equal(st["t"][sl], sr["t"])
+        assert np.all(sr["t"] == t_end)
+        for f in ("x", "v"):
+            assert rel_err(st[f][sl], sr[f]).max() < tol_xv, (k, f, rel_err(st[f][sl], sr[f]).max())
+        kap = O.evaluate_kappa(ms[k], sr["x"], sr["v"], sr["a"], eps)
+        at_ref = O.evaluate(ms[k], sr["x"], sr["v"], sr["a"], eps)
+        at_gpu = O.evaluate(ms[k], st["x"][sl], st["v"][sl], st["a"][sl], eps)
+        for q, (f, kq) in enumerate(zip(("a", "j", "s"), kap)):
+            drift = np.abs(at_gpu[q] - at_ref[q]).max(axis=1)
+            err = np.abs(st[f][sl] - sr[f]).max(axis=1)
+            assert np.all(err <= 1e-6 * kq + 2.0 * drift), (k, f, (err / (1e-6 * kq + 2 * drift)).max())
+    assert small > 0 and large > 0      # both evaluation paths of the persistent kernel ran
+
+
 def test_mixed_ensemble_tracks_fp64_and_conserves_energy():
     nb = nb_gpu()
     sizes = [300, 1000, 64]
     ms, xs, vs = _systems(sizes, 80)
     eps, t_end = 1e-4, 0.125
     res = {}
-    for prec in (nb.NB_FP64, nb.NB_MIXED):
+    for prec in (nb.NB_FP64, nb.NB_MIXED, nb.NB_MIXED32):
         ens = nb.Ensemble(sizes, *_concat(ms, xs, vs), eps, precision=prec)
         ens.run(t_end)
         res[prec] = ens.state()
@@ -82,11 +140,12 @@ def test_mixed_ensemble_tracks_fp64_and_conserves_energy():
     o = 0
     for k, n in enumerate(sizes):
         e0 = sum(O.energy(ms[k], xs[k], vs[k], eps))
-        for prec in (nb.NB_FP64, nb.NB_MIXED):
+        for prec in (nb.NB_FP64, nb.NB_MIXED, nb.NB_MIXED32):
             st = res[prec]
             e1 = sum(O.energy(ms[k], st["x"][o:o + n], st["v"][o:o + n], eps))
             assert abs((e1 - e0) / e0) < 1e-8, (k, prec)
-        assert rel_err(res[nb.NB_MIXED]["x"][o:o + n], res[nb.NB_FP64]["x"][o:o + n]).max() < 1e-6
+        for prec in (nb.NB_MIXED, nb.NB_MIXED32):
+            assert rel_err(res[prec]["x"][o:o + n], res[nb.NB_FP64]["x"][o:o + n]).max() < 1e-6
         o += n
 
 
@@ -130,7 +189,7 @@ def test_ex_ensemble_launch_shapes_agree_and_track_fp64():
         np.testing.assert_array_equal(st["t"], st64["t"])
 
 
-@pytest.mark.parametrize("prec", [0, 1, 3])
+@pytest.mark.parametrize("prec", [0, 1, 3, 4])
 def test_lone_particle_system_coasts_at_the_largest_step(prec):
     """A one-particle system feels no force: its step criterion is 0/0 and
     sets no bound, so it coasts in a straight line at dt_max (exactly, with

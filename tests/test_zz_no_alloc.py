@@ -34,7 +34,8 @@ def _records(xp, vp, ap, m):
     return rec
 
 
-@pytest.mark.parametrize("n,n_act,split", [(3000, 5, 0), (3000, 700, 0), (4099, 64, 9)])
+@pytest.mark.parametrize("n,n_act,split", [(3000, 5, 0), (3000, 700, 0), (4099, 64, 9),
+                                           (1 << 17, 1 << 17, 0)])
 def test_static_scratch_entry_matches_context_path_twice(n, n_act, split):
     nb = nb_gpu()
     import torch
@@ -53,13 +54,18 @@ def test_static_scratch_entry_matches_context_path_twice(n, n_act, split):
     act_d = torch.from_numpy(act).cuda()
     stream = torch.cuda.current_stream().cuda_stream
     lib = nb.lib()
-    for call in range(2):
-        out = torch.full((9, n_act), float("nan"), dtype=torch.float64, device="cuda")
+    # two calls queued back to back on one stream (no synchronisation between
+    # them): work on one stream runs in order, so the second call's clearing
+    # of the shared scratch cannot overtake the first call's use of it
+    outs = [torch.full((9, n_act), float("nan"), dtype=torch.float64, device="cuda")
+            for _ in range(2)]
+    for out in outs:
         st = lib.nb_evaluate_fp64_static(C.c_void_p(rec.data_ptr()), n, C.c_void_p(act_d.data_ptr()),
                                          n_act, eps, split, C.c_void_p(out.data_ptr()),
                                          C.c_void_p(stream))
         assert st == nb.NB_OK, lib.nb_last_error(None)
-        torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    for call, out in enumerate(outs):
         got = out.cpu().numpy()
         for q in range(3):
             g = got[3 * q:3 * q + 3].T

@@ -24,8 +24,12 @@
 // dbeta/dv = 2 q^2 (v + alpha r), dbeta/da = q^2 r.
 // Particle k receives -dL/d(r, v, a) of every pair where it is i (with its
 // own cotangents) and +dL/d(r, v, a) and dL/dm of every pair where it is j
-// (with the other particle's cotangents); one thread owns k and visits every
-// l once, so no atomics are needed.
+// (with the other particle's cotangents).  `lanes` consecutive threads own
+// k and visit every l once between them (every lanes-th l of each tile);
+// their sums are combined by a fixed-order butterfly of warp shuffles, so
+// no atomics are needed and the result does not depend on scheduling.  The
+// lanes keep small systems from leaving most SMs idle (one thread per k
+// would give 64 blocks for 8192 particles).
 #include <algorithm>
 
 #include "nb_device.cuh"
@@ -73,7 +77,7 @@ __device__ __forceinline__ void pair_bracket(const double (&r)[3], const double 
 // first pair's form evaluated at (r, v, a) with l's cotangents; by linearity
 // both roles need one bracket with g* = m_k g_l - m_l g_k, times q^3.  The mass
 // gradient of m_k is -q^3 Phi(g_l).  For l = k, g* = 0 and Phi = 0 exactly.
-__global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(int n, const double *__restrict__ m,
+__global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(int n, int lanes, const double *__restrict__ m,
                                                               const double *__restrict__ x,
                                                               const double *__restrict__ v,
                                                               const double *__restrict__ a,
@@ -85,7 +89,8 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(int n, const doubl
 {
     __shared__ double s_st[kAdjTile][10];  // x, v, a, m
     __shared__ double s_g[kAdjTile][9];    // cotangents
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slot = threadIdx.x / lanes, lj = threadIdx.x - slot * lanes;
+    const int k = blockIdx.x * (blockDim.x / lanes) + slot;
     const bool valid = k < n;
     const int kk = valid ? k : 0;
     double xk[3], vk[3], ak[3], gk[9];
@@ -117,7 +122,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(int n, const doubl
         }
         __syncthreads();
         const int len = min(kAdjTile, n - l0);
-        for (int e = 0; e < len; ++e) {
+        for (int e = lj; e < len; e += lanes) {
             double r[3], vr[3], ar[3];
             for (int d = 0; d < 3; ++d) {
                 r[d] = s_st[e][d] - xk[d];
@@ -153,7 +158,15 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(int n, const doubl
             om = fma(-q3, phil, om);
         }
     }
-    if (valid) {
+    for (int off = lanes >> 1; off > 0; off >>= 1) {
+        for (int d = 0; d < 3; ++d) {
+            ox[d] += __shfl_xor_sync(0xffffffffu, ox[d], off);
+            ov[d] += __shfl_xor_sync(0xffffffffu, ov[d], off);
+            oa[d] += __shfl_xor_sync(0xffffffffu, oa[d], off);
+        }
+        om += __shfl_xor_sync(0xffffffffu, om, off);
+    }
+    if (valid && lj == 0) {
         for (int d = 0; d < 3; ++d) {
             gx[3 * k + d] = ox[d];
             gv[3 * k + d] = ov[d];
@@ -260,9 +273,22 @@ nb_status nb_pairs_fp64_adjoint(int64_t n, const double *m, const double *x, con
     }
     const int nn = static_cast<int>(n);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    adjoint_kernel<<<(nn + kAdjThreads - 1) / kAdjThreads, kAdjThreads, 0, s>>>(
-        nn, m, x, v, a, gacc, gjerk, gsnap, eps * eps, gx, gv, ga, gm);
-    const cudaError_t e = cudaGetLastError();
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        nb_set_thread_error(cudaGetErrorString(e));
+        return NB_ECUDA;
+    }
+    // lanes per particle: the fewest that give every SM at least four blocks
+    int lanes = 1;
+    while (lanes < 32 && (static_cast<int64_t>(nn) * lanes + kAdjThreads - 1) / kAdjThreads < 4 * sms)
+        lanes *= 2;
+    const int per_block = kAdjThreads / lanes;
+    adjoint_kernel<<<(nn + per_block - 1) / per_block, kAdjThreads, 0, s>>>(
+        nn, lanes, m, x, v, a, gacc, gjerk, gsnap, eps * eps, gx, gv, ga, gm);
+    e = cudaGetLastError();
     if (e != cudaSuccess) {
         nb_set_thread_error(cudaGetErrorString(e));
         return NB_ECUDA;

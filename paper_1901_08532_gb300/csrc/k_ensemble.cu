@@ -12,7 +12,8 @@
 //             counts meet through distributed shared memory);
 //   predict   each CTA its slice: for small active sets straight into
 //             shared memory, otherwise into the system's evaluation buffer;
-//   evaluate  small active sets (<= kSmall): every CTA evaluates the whole
+//   evaluate  small active sets (<= kSmall, and at most one per thread):
+//             every CTA evaluates the whole
 //             set against its own slice and the owner of each active
 //             particle adds the CTAs' partial sums in rank order (two cluster
 //             barriers per block step); larger sets: each CTA a share of the
@@ -606,7 +607,10 @@ __device__ void correct_share(const EnsArgs &a, int off, int s0, int s1, double 
 // against its own slice of the system, just predicted by itself, and leaves
 // 9 partial sums per active particle in shared memory; the block that owns
 // a particle adds the cluster's partials in rank order and corrects it.
-constexpr int kSmall = 16;
+// Up to 128 (and at most the block's thread count): with more active
+// particles than CTAs, handing whole particles to CTAs (the large-set path)
+// leaves CTAs and warps idle; here every CTA works on its own j-slice.
+constexpr int kSmall = 128;
 
 // i-values of the small active set: FP64 x, v, a; in mixed precision the
 // same slots hold 12 negated FP32 values (x_hi, x_lo, v, a) of the record the
@@ -1027,7 +1031,8 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
             const int mine = (mt == mb) ? ct : 0;
             int tot_b = 0;
             const int ex = block_exclusive_scan(mine, red_i, &tot_b);
-            if (mine > 0 && tot_b <= kSmall) {
+            const int small_max = min(kSmall, T);
+            if (mine > 0 && tot_b <= small_max) {
                 int pos = ex;
                 for (int i = c0; i < c1; ++i)
                     if (a.t[i] + a.dt[i] == mb)
@@ -1052,7 +1057,7 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
                 prefix += r < rank ? v : 0;
                 total += v;
             }
-            if (total <= kSmall) {
+            if (total <= small_max) {
                 // active list in ascending order from the blocks' lists, and
                 // its predicted values (the arithmetic of the j-records)
                 if (tid < G) {

@@ -68,28 +68,34 @@ def test_fp64_ensemble_launch_shapes_agree():
         np.testing.assert_array_equal(st["t"], out[0]["t"])
 
 
-@pytest.mark.parametrize("prec, tol_xv", [(1, 1e-9), (4, 1e-7)])
+@pytest.mark.parametrize("prec, tol_xv", [(1, 1e-8), (4, 1e-7)])
 def test_mixed_ensembles_match_oracle_replay_per_system(prec, tol_xv):
     """Mixed ensembles against the FP64 oracle, system by system.  FP32 pair
     arithmetic may move a step decision across a power of two (another valid
     trajectory), so the oracle replays each system's logged (t_next, active
-    set) sequence from the ensemble's own starting state; then t must agree
-    exactly, x and v per particle to tol_xv of |x|, |v|, and a, jerk and
-    snap to 1e-6 of each sum's condition number sum_j |T_ij| plus twice the
-    change the oracle's own sums show between the two final states (the
-    inputs differ: positions by the accumulated force rounding, and the
-    snap's a_j - a_i by the mixed accelerations of the previous steps).
-    Every particle is evaluated at t_end in the last step.  NB_MIXED (1)
-    predicts and corrects in FP64: 1e-9.  NB_MIXED32 (4) forms the
-    corrector's increments in FP32 (about 6e-8 of each increment): 1e-7.
-    The run is short (to t = 2^-10, block steps down to 2^-20), since the
-    per-step force rounding of a few 1e-8 grows along close encounters."""
+    set) sequence, starting from its own start-up state (only the step
+    decisions come from the GPU); then t must agree exactly, x and v per
+    particle to tol_xv of |x|, |v|, and a and jerk to 1e-6 of each sum's
+    condition number sum_j |T_ij| (on the oracle's final state; every
+    particle is evaluated at t_end in the last step).  Snap takes the
+    predicted accelerations as inputs, and their crackle term comes from the
+    quintic interpolation, which divides the rounding of a, jerk and snap by
+    h^3 (60 R1 / h^3) before the predictor multiplies it back by h^3 / 6:
+    the predicted a carries about ten times the evaluation's relative
+    rounding, so snap is held to 1e-5 of its condition number.
+    The two start-up states differ by the mixed rounding of the starting
+    forces (about 1e-7 of |a|), which the integration carries into v (|a| t
+    of a few 1e-9 of |v| for the 5-body system's close pair at t = 2^-10):
+    NB_MIXED (1), whose predictor and corrector are FP64, is held to 1e-8 in
+    x and v; NB_MIXED32 (4) forms the corrector's increments in FP32 (about
+    6e-8 of each increment): 1e-7.  The run is short (to t = 2^-10, block
+    steps down to 2^-20), since the per-step force rounding of a few 1e-8
+    grows along close encounters."""
     nb = nb_gpu()
     sizes = [2, 5, 16, 33, 300, 64, 257]
     ms, xs, vs = _systems(sizes, 110)
     eps, t_end = 1e-4, 2.0 ** -10
     ens = nb.Ensemble(sizes, *_concat(ms, xs, vs), eps, precision=prec, dt_max=t_end)
-    st0 = ens.state()
     ens.set_log(1 << 20, 1 << 24)
     ens.run(t_end)
     st = ens.state()
@@ -109,7 +115,6 @@ def test_mixed_ensembles_match_oracle_replay_per_system(prec, tol_xv):
         small += sum(len(q) <= 16 for q in sets)
         large += sum(len(q) > 16 for q in sets)
         ref = O.System(ms[k], xs[k], vs[k], eps, dt_max=t_end)
-        ref.set_state({f: st0[f][sl] for f in ("x", "v", "a", "j", "s", "c", "t", "dt")})
         ref.replay(tn, sets)
         sr = ref.state()
         np.testing.assert_array_equal(st["t"][sl], sr["t"])
@@ -117,12 +122,9 @@ def test_mixed_ensembles_match_oracle_replay_per_system(prec, tol_xv):
         for f in ("x", "v"):
             assert rel_err(st[f][sl], sr[f]).max() < tol_xv, (k, f, rel_err(st[f][sl], sr[f]).max())
         kap = O.evaluate_kappa(ms[k], sr["x"], sr["v"], sr["a"], eps)
-        at_ref = O.evaluate(ms[k], sr["x"], sr["v"], sr["a"], eps)
-        at_gpu = O.evaluate(ms[k], st["x"][sl], st["v"][sl], st["a"][sl], eps)
-        for q, (f, kq) in enumerate(zip(("a", "j", "s"), kap)):
-            drift = np.abs(at_gpu[q] - at_ref[q]).max(axis=1)
-            err = np.abs(st[f][sl] - sr[f]).max(axis=1)
-            assert np.all(err <= 1e-6 * kq + 2.0 * drift), (k, f, (err / (1e-6 * kq + 2 * drift)).max())
+        for f, kq in zip(("a", "j", "s"), kap):
+            tol = 1e-5 if f == "s" else 1e-6
+            assert check_parity(1, st[f][sl], sr[f], kq, tol_mixed=tol) <= 1.0, (k, f)
     assert small > 0 and large > 0      # both evaluation paths of the persistent kernel ran
 
 

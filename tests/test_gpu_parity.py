@@ -144,14 +144,12 @@ def test_fp64_block_steps_take_the_oracles_decisions():
 def test_mixed_block_steps_against_oracle_replay():
     """Mixed: FP32 rounding may move a step-size decision across a power of
     two, which gives another valid trajectory.  The oracle replays the GPU's
-    decisions (t_next and active sets) from the same start and the states
-    are compared."""
+    decisions (t_next and active sets) from its own start-up state (the same
+    positions and velocities) and the states are compared."""
     nb = nb_gpu()
     m, x, v = ni.plummer(300, 4)
     g = nb.NBody(m, x, v, 1e-4, precision=nb.NB_MIXED)
-    st0 = g.state()
-    ref = O.System(m, x, v, 1e-4)
-    ref.set_state(st0)
+    ref = O.System(m, x, v, 1e-4)     # its own start-up; only the decisions come from the GPU
     tn, sets = [], []
     for _ in range(4):
         t_g, n_g = g.step()
@@ -334,20 +332,22 @@ def test_full_size_sampled_parity(prec):
 def test_bench_headline_launch_sampled_parity():
     """The bench's headline step: N = 2^20 Plummer with Salpeter masses,
     eps = 1e-4, every particle active, the mixed kernel in the automatic
-    launch shape (KI 2, 128 threads, j-tile 512, no split), on the start-up
-    state the bench uses; 32 evenly spread particles against the oracle."""
+    launch shape (KI 3, 128 threads, j-tile 512, no split), with the seeded
+    acceleration field the bench's oracle comparison uses; 32 evenly spread
+    particles against the oracle."""
     nb = nb_gpu()
     n, eps = 1 << 20, 1e-4
     m, x, v = ni.plummer(n, 3, imf="salpeter")
-    g = nb.NBody(m, x, v, eps, precision=nb.NB_MIXED, dt_shared=2.0 ** -10)
-    st = g.state()
+    a = ni.random_state(n, 5, scale=2.0)
+    g = nb.NBody(m, x, v, eps, precision=nb.NB_MIXED, dt_shared=2.0 ** -10, start_forces=False)
+    g.set_state({"a": a})
     shape = g.resolve_tiles(n)
-    assert (shape["ki"], shape["threads"], shape["jtile"], shape["split"]) == (2, 128, 512, 1)
+    assert (shape["ki"], shape["threads"], shape["jtile"], shape["split"]) == (3, 128, 512, 1)
     g.predict(0.0)
     got = g.evaluate(None)
     g.close()
     pick = np.linspace(0, n - 1, 32).astype(np.int32)
-    ref = O.evaluate(m, x, v, st["a"], eps, pick)
-    kap = O.evaluate_kappa(m, x, v, st["a"], eps, pick)
+    ref = O.evaluate(m, x, v, a, eps, pick)
+    kap = O.evaluate_kappa(m, x, v, a, eps, pick)
     for gq, rq, kq in zip(got, ref, kap):
         assert check_parity(1, gq[pick], rq, kq) <= 1.0

@@ -12,7 +12,7 @@
 //             counts meet through distributed shared memory);
 //   predict   each CTA its slice: for small active sets straight into
 //             shared memory, otherwise into the system's evaluation buffer;
-//   evaluate  small active sets (<= kSmall, and at most one per thread):
+//   evaluate  small active sets (<= small_set(PR), at most one per thread):
 //             every CTA evaluates the whole
 //             set against its own slice and the owner of each active
 //             particle adds the CTAs' partial sums in rank order (two cluster
@@ -59,6 +59,9 @@ struct nb_ensemble {
     double2 *jb64 = nullptr;
     float *jf32 = nullptr;
     float *st32 = nullptr;  // NB_MIXED32: FP32 copy of the state [24][P] (rows: see predict_one_mixed)
+    double *gpart = nullptr;  // j-split partial sums, [clusters in the grid][G][9][nmax4]
+    size_t gpart_cap = 0;     // doubles
+    int64_t nmax4 = 4;        // largest system, padded to a multiple of 4
     // optional step log (nb_ensemble_set_log): counters [2] = steps, indices
     unsigned long long *log_cnt = nullptr;
     int32_t *log_sys = nullptr, *log_n = nullptr, *log_idx = nullptr;
@@ -98,6 +101,8 @@ struct EnsArgs {
     int64_t *steps;
     unsigned long long *inter;
     nb_ctl *ctl;
+    double *gpart;                 // j-split partial sums: [clusters][G][9][gstride]
+    long long gstride;             // largest system, padded to a multiple of 4
     unsigned long long *log_cnt;   // NULL: no step log
     int32_t *log_sys, *log_n, *log_idx;
     double *log_t;
@@ -310,21 +315,23 @@ __device__ __forceinline__ void issue_ens_tile(const EnsArgs &a, unsigned char *
 }
 
 // Evaluate active slots [s0, s1) of the system starting at `off` against its
-// nj j-records.  Returns false if a TMA wait timed out (uniform in the CTA).
+// j-records [j0, j1) (local indices; j0 a multiple of 4), writing the sums of
+// slot p to out[q * ostride + p].  The slots go in rounds of at most one per
+// thread; a round with fewer slots than threads gives each slot `lanes`
+// threads that split its j-tiles, so the last round of a large set and a
+// small set keep the block busy (an idle slot would repeat a particle on
+// the slow FP64 pipe).  Returns false if a TMA wait timed out (uniform in
+// the CTA).
 template <int PR>
-__device__ bool eval_share(const EnsArgs &a, int off, int nj, int s0, int s1, unsigned char *smem,
-                           uint64_t *bar, unsigned &seq)
+__device__ bool eval_share(const EnsArgs &a, int off, int j0, int j1, int s0, int s1, double *out,
+                           size_t ostride, unsigned char *smem, uint64_t *bar, unsigned &seq)
 {
     [[maybe_unused]] constexpr bool MIXED = PR == 1 || PR == 3, EXP = PR == 2;
     const int T = blockDim.x, tid = threadIdx.x, jt = a.jtile;
-    const int m = s1 - s0;
-    if (m <= 0)
+    if (s1 <= s0)
         return true;
     const size_t P = static_cast<size_t>(a.P);
-    int lanes = 1;
-    while (lanes < 32 && (T / (2 * lanes)) >= m)
-        lanes *= 2;
-    const int slots = T / lanes, slot = tid / lanes, lj = tid - slot * lanes;
+    const int nj = j1 - j0;
     const int ntiles = (nj + jt - 1) / jt;
     constexpr int kRow[12] = {0, 1, 2, 4, 5, 6, 7, 8, 9, 10, 11, 12};
     // the j-records were written by other blocks of the cluster (generic
@@ -332,7 +339,11 @@ __device__ bool eval_share(const EnsArgs &a, int off, int nj, int s0, int s1, un
     if (tid == 0)
         asm volatile("fence.proxy.async.global;" ::: "memory");
 
-    for (int ib = s0; ib < s1; ib += slots) {
+    for (int ib = s0; ib < s1;) {
+        int lanes = 1;
+        while (lanes < 32 && (T / (2 * lanes)) >= s1 - ib)
+            lanes *= 2;
+        const int slots = T / lanes, slot = tid / lanes, lj = tid - slot * lanes;
         const int p = ib + slot;
         const bool valid = p < s1;
         const int i = a.act[off + (valid ? p : s1 - 1)];
@@ -367,7 +378,7 @@ __device__ bool eval_share(const EnsArgs &a, int off, int nj, int s0, int s1, un
         }
         if (tid == 0)
             for (int q = 0; q < min(2, ntiles); ++q)
-                issue_ens_tile<PR>(a, smem, bar, (seq + q) & 1, off + q * jt, min(jt, nj - q * jt));
+                issue_ens_tile<PR>(a, smem, bar, (seq + q) & 1, off + j0 + q * jt, min(jt, nj - q * jt));
         for (int tl = 0; tl < ntiles; ++tl) {
             const unsigned sq = seq + tl;
             const int stg = sq & 1;
@@ -435,7 +446,7 @@ __device__ bool eval_share(const EnsArgs &a, int off, int nj, int s0, int s1, un
             }
             __syncthreads();
             if (tid == 0 && tl + 2 < ntiles)
-                issue_ens_tile<PR>(a, smem, bar, stg, off + (tl + 2) * jt, min(jt, nj - (tl + 2) * jt));
+                issue_ens_tile<PR>(a, smem, bar, stg, off + j0 + (tl + 2) * jt, min(jt, nj - (tl + 2) * jt));
         }
         seq += ntiles;
         if (MIXED)
@@ -449,7 +460,8 @@ __device__ bool eval_share(const EnsArgs &a, int off, int nj, int s0, int s1, un
         if (valid && lj == 0)
 #pragma unroll
             for (int q = 0; q < 9; ++q)
-                a.anew[static_cast<size_t>(q) * P + off + p] = acc[q];
+                out[static_cast<size_t>(q) * ostride + p] = acc[q];
+        ib += slots;
     }
     return true;
 }
@@ -587,30 +599,19 @@ __device__ __forceinline__ void correct_particle(const EnsArgs &a, int i, double
         correct_one(a, i, tn, f);
 }
 
-// Corrector for active slots [s0, s1) at time tn (new values in anew).
-template <int PR>
-__device__ void correct_share(const EnsArgs &a, int off, int s0, int s1, double tn)
-{
-    [[maybe_unused]] constexpr bool MIXED = PR == 1 || PR == 3, EXP = PR == 2;
-    const size_t P = static_cast<size_t>(a.P);
-    for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
-        double f[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q)
-            f[q] = a.anew[q * P + off + k];
-        correct_particle<PR>(a, a.act[off + k], tn, f);
-    }
-}
-
-// Small active sets (at most kSmall particles, the usual case once close
+// Small active sets (at most small_set(PR) particles, the usual case once close
 // pairs sit at small steps): every block evaluates the whole active set
 // against its own slice of the system, just predicted by itself, and leaves
 // 9 partial sums per active particle in shared memory; the block that owns
 // a particle adds the cluster's partials in rank order and corrects it.
-// Up to 128 (and at most the block's thread count): with more active
-// particles than CTAs, handing whole particles to CTAs (the large-set path)
-// leaves CTAs and warps idle; here every CTA works on its own j-slice.
-constexpr int kSmall = 128;
+// FP64 and EX: up to 128 (and at most the block's thread count), so that
+// moderate sets also take this path, where every CTA works on its own
+// j-slice and the i-values sit in shared memory.  Mixed: 16, which keeps
+// the static shared memory small beside the mixed path's long j-tiles (two
+// blocks per SM); its steps with more active particles take the j-split
+// large-set path, which is as well balanced.
+constexpr int kSmallMax = 128;
+__host__ __device__ constexpr int small_set(int pr) { return pr == 1 || pr == 3 ? 16 : kSmallMax; }
 
 // i-values of the small active set: FP64 x, v, a; in mixed precision the
 // same slots hold 12 negated FP32 values (x_hi, x_lo, v, a) of the record the
@@ -955,11 +956,12 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
     __shared__ int s_fail;
     __shared__ double s_min2[2];
     __shared__ int s_cnt2[2];
-    __shared__ int s_cand[2][kSmall];
-    __shared__ int s_act[kSmall];
+    constexpr int KS = small_set(PR);
+    __shared__ int s_cand[2][KS];
+    __shared__ int s_act[KS];
     __shared__ int s_rcnt[kMaxCluster];
-    __shared__ double s_iv[kSmall][9];
-    __shared__ double s_part[kSmall][9];
+    __shared__ double s_iv[KS][9];
+    __shared__ double s_part[KS][9];
     __shared__ double s_wred[kEnsThreads / 32][9];
     __shared__ long long s_log_ip;
     cg::cluster_group cl = cg::this_cluster();
@@ -998,7 +1000,8 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
             for (int pass = 0; pass < 2; ++pass) {
                 predict_slice<PR>(a, lo, hi, 0.0);
                 cl.sync();
-                const bool ok = eval_share<PR>(a, off, nj, lo - off, hi - off, smem, bar, seq);
+                const bool ok = eval_share<PR>(a, off, 0, nj, lo - off, hi - off, a.anew + off,
+                                               static_cast<size_t>(a.P), smem, bar, seq);
                 if (!ok && tid == 0)
                     s_fail = 1;
                 __syncthreads();
@@ -1031,7 +1034,7 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
             const int mine = (mt == mb) ? ct : 0;
             int tot_b = 0;
             const int ex = block_exclusive_scan(mine, red_i, &tot_b);
-            const int small_max = min(kSmall, T);
+            const int small_max = min(KS, T);
             if (mine > 0 && tot_b <= small_max) {
                 int pos = ex;
                 for (int i = c0; i < c1; ++i)
@@ -1106,14 +1109,35 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_kernel(EnsArgs a)
                 cl.sync();
                 if (a.log_cnt && rank == 0)
                     log_step(a, c, tn, total, a.act + off, off, &s_log_ip);
-                const int q = (total + G - 1) / G;
-                const int s0 = min(total, rank * q), s1 = min(total, s0 + q);
-                const bool ok = eval_share<PR>(a, off, nj, s0, s1, smem, bar, seq);
+                // j-split: this block's share of the j-records (4-aligned)
+                // against every active particle, partial sums to the
+                // cluster's scratch; then each block adds, in rank order,
+                // the partials of its share of the active particles and
+                // corrects them
+                const int per4 = ((nj + G - 1) / G + 3) / 4 * 4;
+                const int jl = min(nj, rank * per4), jh = min(nj, jl + per4);
+                const size_t gs = static_cast<size_t>(a.gstride);
+                double *gcl = a.gpart + static_cast<size_t>(blockIdx.x / G) * G * 9 * gs;
+                const bool ok = eval_share<PR>(a, off, jl, jh, 0, total, gcl + rank * 9 * gs, gs, smem, bar, seq);
                 if (!ok && tid == 0)
                     s_fail = 1;
-                __syncthreads();
-                if (ok)
-                    correct_share<PR>(a, off, s0, s1, tn);
+                cl.sync();
+                int bad = 0;
+                for (int r = 0; r < G; ++r)
+                    bad |= *cl.map_shared_rank(&s_fail, r);
+                const int q = (total + G - 1) / G;
+                const int s0 = min(total, rank * q), s1 = min(total, s0 + q);
+                for (int k = s0 + tid; k < s1 && !bad; k += T) {
+                    double f[9];
+#pragma unroll
+                    for (int u = 0; u < 9; ++u)
+                        f[u] = 0.0;
+                    for (int r = 0; r < G; ++r)
+#pragma unroll
+                        for (int u = 0; u < 9; ++u)
+                            f[u] += gcl[(static_cast<size_t>(r) * 9 + u) * gs + k];
+                    correct_particle<PR>(a, a.act[off + k], tn, f);
+                }
                 cl.sync();
             }
             ++steps;
@@ -1270,6 +1294,8 @@ EnsArgs make_args(nb_ensemble *e, int mode, double t_end)
     a.steps = e->steps;
     a.inter = e->inter;
     a.ctl = e->ctl;
+    a.gpart = e->gpart;
+    a.gstride = e->nmax4;
     a.log_cnt = e->log_cnt;
     a.log_sys = e->log_sys;
     a.log_n = e->log_n;
@@ -1290,15 +1316,37 @@ EnsArgs make_args(nb_ensemble *e, int mode, double t_end)
     return a;
 }
 
-// Enqueue one persistent launch (queue reset + kernel) on e->stream.
-nb_status enqueue_run(nb_ensemble *e, int mode, double t_end)
+// Clusters in the grid (at most the number the device co-schedules, at most
+// one per system) and the j-split scratch for them; call outside stream
+// capture (it may allocate).
+nb_status prepare_grid(nb_ensemble *e, int *grid)
 {
     int maxc = 0;
-    const int kind = ens_kind(e);
     ECU(e, max_clusters_kind(e, &maxc));
     if (maxc < 1)
         return efail(e, NB_EINVAL, "ensemble launch shape does not fit on an SM");
-    const int grid = std::min(maxc, e->nc);
+    *grid = std::min(maxc, e->nc);
+    const size_t need = static_cast<size_t>(*grid) * e->G * 9 * static_cast<size_t>(e->nmax4);
+    if (need > e->gpart_cap) {
+        cudaFree(e->gpart);
+        e->gpart = nullptr;
+        e->gpart_cap = 0;
+        const cudaError_t c = cudaMalloc(&e->gpart, need * sizeof(double));
+        if (c == cudaErrorMemoryAllocation) {
+            (void)cudaGetLastError();
+            return efail(e, NB_ENOMEM, "no device memory for the ensemble's partial sums");
+        }
+        ECU(e, c);
+        e->gpart_cap = need;
+    }
+    return NB_OK;
+}
+
+// Enqueue one persistent launch (queue reset + kernel) on e->stream; the
+// grid was prepared by prepare_grid.
+nb_status enqueue_run(nb_ensemble *e, int mode, double t_end, int grid)
+{
+    const int kind = ens_kind(e);
     ECU(e, cudaMemsetAsync(e->queue, 0, sizeof(int), e->stream));
     const EnsArgs a = make_args(e, mode, t_end);
     cudaError_t le;
@@ -1344,6 +1392,7 @@ void ens_free_all(nb_ensemble *e)
     cudaFree(e->jb64);
     cudaFree(e->jf32);
     cudaFree(e->st32);
+    cudaFree(e->gpart);
     cudaFree(e->log_cnt);
     cudaFree(e->log_sys);
     cudaFree(e->log_n);
@@ -1467,6 +1516,8 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
             o += (sizes[c] + 3) / 4 * 4;
         }
     }
+    for (int c = 0; c < n_systems; ++c)
+        e->nmax4 = std::max<int64_t>(e->nmax4, (e->cnt[c] + 3) / 4 * 4);
     std::vector<int32_t> order(n_systems);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(),
@@ -1538,7 +1589,10 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
     EI(cudaMemsetAsync(e->steps, 0, n_systems * sizeof(int64_t), e->stream));
     EI(cudaMemsetAsync(e->inter, 0, sizeof(unsigned long long), e->stream));
     EI(cudaMemsetAsync(e->ctl, 0, sizeof(nb_ctl), e->stream));
-    nb_status s = enqueue_run(e, 1, 0.0);
+    int grid = 0;
+    nb_status s = prepare_grid(e, &grid);
+    if (s == NB_OK)
+        s = enqueue_run(e, 1, 0.0, grid);
     if (s != NB_OK)
         return bail(s);
     e->launches += 1;
@@ -1589,7 +1643,10 @@ nb_status nb_ensemble_run(nb_ensemble *e, double t_end, int use_graph)
     if (!std::isfinite(t_end) || t_end < 0.0 || std::fmod(t_end, unit) != 0.0)
         return efail(e, NB_EINVAL, "t_end must be a non-negative multiple of dt_max (dt_shared)");
     if (!use_graph) {
-        nb_status s = enqueue_run(e, 0, t_end);
+        int grid = 0;
+        nb_status s = prepare_grid(e, &grid);
+        if (s == NB_OK)
+            s = enqueue_run(e, 0, t_end, grid);
         if (s != NB_OK)
             return s;
         e->launches += 1;
@@ -1604,11 +1661,13 @@ nb_status nb_ensemble_run(nb_ensemble *e, double t_end, int use_graph)
             cudaGraphDestroy(e->graph);
             e->graph = nullptr;
         }
-        // occupancy query and attributes before capture
-        int maxc = 0;
-        ECU(e, max_clusters_kind(e, &maxc));
+        // occupancy query, attributes and scratch before capture
+        int grid = 0;
+        nb_status s = prepare_grid(e, &grid);
+        if (s != NB_OK)
+            return s;
         ECU(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
-        nb_status s = enqueue_run(e, 0, t_end);
+        s = enqueue_run(e, 0, t_end, grid);
         cudaGraph_t g = nullptr;
         cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
         if (s != NB_OK) {

@@ -119,6 +119,12 @@ __device__ __forceinline__ void store_or_fold(const EvalArgs &a, double (&acc)[9
 
 // ------------------------------------------------------------------ FP64
 
+// With four i-particles per thread the running totals (9 x KI doubles,
+// touched once per tile) live in shared memory after the tiles, rows
+// [9 * KI][threads]: in registers they would not fit beside the tile partial
+// sums and the i-values (255 registers per thread at most).
+__host__ __device__ constexpr bool fp64_shared_totals(int ki) { return ki >= 4; }
+
 template <int KI>
 __global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs a)
 {
@@ -131,9 +137,12 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs
     const int ibase = blockIdx.x * slots * KI;
     const double2 *jb = static_cast<const double2 *>(a.jb);
 
+    constexpr bool SH = fp64_shared_totals(KI);
     int kidx[KI];
     double xi[KI], yi[KI], zi[KI], vxi[KI], vyi[KI], vzi[KI], axi[KI], ayi[KI], azi[KI];
-    double acc[9][KI], part[9][KI];
+    double acc[9][SH ? 1 : KI], part[9][KI];
+    double *acc_s = reinterpret_cast<double *>(smem) + static_cast<size_t>(2) * NC * 2 * jt;
+    const int nthr = blockDim.x;
 #pragma unroll
     for (int k = 0; k < KI; ++k) {
         const int p = ibase + slot + k * slots;
@@ -145,8 +154,12 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs
         vxi[k] = r2.x; vyi[k] = r2.y; vzi[k] = r3.x;
         axi[k] = r3.y; ayi[k] = r4.x; azi[k] = r4.y;
 #pragma unroll
-        for (int q = 0; q < 9; ++q)
-            acc[q][k] = 0.0;
+        for (int q = 0; q < 9; ++q) {
+            if (SH)
+                acc_s[(q * KI + k) * nthr + tid] = 0.0;
+            else
+                acc[q][SH ? 0 : k] = 0.0;
+        }
     }
 
     const int jbeg = a.j0 + blockIdx.y * a.jchunk;
@@ -198,8 +211,12 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs
 #pragma unroll
         for (int k = 0; k < KI; ++k)
 #pragma unroll
-            for (int q = 0; q < 9; ++q)
-                acc[q][k] += part[q][k];
+            for (int q = 0; q < 9; ++q) {
+                if (SH)
+                    acc_s[(q * KI + k) * nthr + tid] += part[q][k];
+                else
+                    acc[q][SH ? 0 : k] += part[q][k];
+            }
         __syncthreads();
         if (tid == 0 && tl + 2 < ntiles) {
             issue_tile<NC>(smem, bar, a, st, jbeg + (tl + 2) * jt, min(jt, jend - (jbeg + (tl + 2) * jt)));
@@ -207,13 +224,19 @@ __global__ void __launch_bounds__(max_threads_for(KI)) eval_fp64_kernel(EvalArgs
         }
     }
 
+    // the totals (from shared memory for SH; the tile partials are dead here)
+#pragma unroll
+    for (int k = 0; k < KI; ++k)
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            part[q][k] = SH ? acc_s[(q * KI + k) * nthr + tid] : acc[q][SH ? 0 : k];
     for (int off = lanes >> 1; off > 0; off >>= 1)
 #pragma unroll
         for (int k = 0; k < KI; ++k)
 #pragma unroll
             for (int q = 0; q < 9; ++q)
-                acc[q][k] += __shfl_xor_sync(0xffffffffu, acc[q][k], off);
-    store_or_fold<KI>(a, acc, kidx, lj, slots, ibase);
+                part[q][k] += __shfl_xor_sync(0xffffffffu, part[q][k], off);
+    store_or_fold<KI>(a, part, kidx, lj, slots, ibase);
 }
 
 // ----------------------------------------------------------------- mixed
@@ -560,7 +583,9 @@ int resident_blocks(const nb_ctx *c, const nb_tiles &t)
     const bool mixed = nb_fp32_eval(c->cfg.precision);
     const bool ex = c->cfg.precision == NB_EX;
     const size_t smem = static_cast<size_t>(2) * (ex ? kRecBytesEx : mixed ? kRecBytes32 : kRecBytes64) * t.jtile +
-                        (mixed ? static_cast<size_t>(18) * t.ki * t.threads * sizeof(float) : 0);
+                        (mixed ? static_cast<size_t>(18) * t.ki * t.threads * sizeof(float) : 0) +
+                        (!mixed && !ex && fp64_shared_totals(t.ki)
+                             ? static_cast<size_t>(9) * t.ki * t.threads * sizeof(double) : 0);
     int nb = 0;
     cudaError_t e;
     if (ex) {
@@ -659,7 +684,9 @@ cudaError_t nb_launch_eval(nb_ctx *c, const EvalLaunch &L)
         return cudaErrorInvalidValue;
     const int rec = ex ? kRecBytesEx : mixed ? kRecBytes32 : kRecBytes64;
     const size_t smem = static_cast<size_t>(2) * rec * t.jtile +
-                        (mixed ? static_cast<size_t>(18) * t.ki * t.threads * sizeof(float) : 0);
+                        (mixed ? static_cast<size_t>(18) * t.ki * t.threads * sizeof(float) : 0) +
+                        (!mixed && !ex && fp64_shared_totals(t.ki)
+                             ? static_cast<size_t>(9) * t.ki * t.threads * sizeof(double) : 0);
     if (smem > 200 * 1024)
         return cudaErrorInvalidValue;
     const int itile = (t.threads / t.lanes) * t.ki;

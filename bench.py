@@ -902,6 +902,8 @@ def ensemble_leg(nb, np, torch, prec_name="ex", t_end=0.25, sample=256):
 
     out = {"workload": f"ensemble_256_plummer_N256-16384_eps1e-4_{prec_name}_t{t_end:g}",
            "systems": int(sizes.size), "particles": int(sizes.sum()), "all": run(list(range(sizes.size)))}
+    if sample <= 0:
+        return out
     order = np.argsort(sizes)
     idx = [int(order[q]) for q in np.linspace(0, sizes.size - 1, sample).astype(int)]
     batched = out["all"] if len(idx) == sizes.size else run(idx)
@@ -925,12 +927,13 @@ def ensemble_leg(nb, np, torch, prec_name="ex", t_end=0.25, sample=256):
 
 def config_legs(nb, np, torch, local):
     """The other configurations, compact, each under its own clock record:
-    the 256-system EX ensemble to t = 1/4 (with the one-at-a-time comparison
-    on 8 systems), the differentiable N = 8192 trajectory (64 steps,
-    checkpoints every 8), and the N = 65536 block-step integration to
-    t = 1/16 in EX and FP64."""
+    the 256-system ensemble to t = 1/4 in EX (with all 256 systems also run
+    one at a time) and in FP64, the differentiable N = 8192 trajectory (64
+    steps, checkpoints every 8), and the N = 65536 block-step integration
+    to t = 1/16 in EX and FP64."""
     legs = {}
     for name, fn in (("ensemble_ex_256", lambda: ensemble_leg(nb, np, torch, "ex")),
+                     ("ensemble_fp64_256", lambda: ensemble_leg(nb, np, torch, "fp64", sample=0)),
                      ("adjoint_n8192", lambda: adjoint_run(torch)),
                      ("integrate_n65536_ex", lambda: integrate_run(nb, np, torch, 65536, "ex")),
                      ("integrate_n65536_fp64", lambda: integrate_run(nb, np, torch, 65536, "fp64"))):

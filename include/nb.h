@@ -335,8 +335,8 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
  * 8 the non-portable cluster size, NB_EINVAL from nb_ensemble_run where the
  * device cannot co-schedule it), threads per block (64..256, multiple of 32),
  * j-tile length (multiple of 4, at most 1024).  0 in a field selects the
- * default: NB_MIXED and NB_MIXED32 4 blocks, j-tile 1024; NB_FP64 and NB_EX 16 blocks where
- * the device co-schedules clusters of 16, else 8, j-tile 256; 128 threads. */
+ * default: NB_MIXED and NB_MIXED32 4 blocks, j-tile 1024; NB_FP64 8 blocks, NB_EX 16 blocks
+ * where the device co-schedules clusters of 16, else 8, j-tile 256; 128 threads. */
 nb_status nb_ensemble_set_shape(nb_ensemble *e, int32_t ctas_per_system, int32_t threads,
                                 int32_t jtile);
 

@@ -117,7 +117,12 @@ bool traj_args_ok(int64_t n, double h)
     return n >= 1 && n <= (int64_t(1) << 40) && h > 0.0 && h <= 1e6 && h >= 1e-12;
 }
 
-int traj_grid(size_t ne) { return static_cast<int>(std::min<size_t>((ne + kTrajThreads - 1) / kTrajThreads, 152 * 16)); }
+// Blocks for ne elements: one element per thread up to 4096 blocks, then
+// grid-stride loops (enough to keep every SM of a large GPU busy).
+int traj_grid(size_t ne)
+{
+    return static_cast<int>(std::min<size_t>((ne + kTrajThreads - 1) / kTrajThreads, 4096));
+}
 
 nb_status launched(const char *what)
 {

@@ -132,7 +132,11 @@ def parse():
                         "equal masses, eps 1e-4, block steps, a device sample every --ps-dt")
     p.add_argument("--ps-t-end", type=float, default=1.0)
     p.add_argument("--ps-dt", type=float, default=2.0 ** -3)
-    p.add_argument("--ps-precs", default="fp64,mixed,ex,sp")
+    p.add_argument("--ps-precs", default="fp64,mixed,ex,sp",
+                   help="comma-separated precisions; name@eps runs it with nb_config.step_noise = eps")
+    p.add_argument("--step-noise", type=float, default=0.0,
+                   help="nb_config.step_noise for --integrate and --ensemble (the rounding floor the "
+                        "step criterion discounts; 0: the criterion as is)")
     p.add_argument("--peaks", action="store_true",
                    help="throughput probes of the CUDA-core pipes (FP32 FMA scalar and f32x2, FP64 "
                         "FMA, special-function estimates, and packed FMAs mixed with estimates)")
@@ -698,7 +702,7 @@ def ensemble_bench(args):
 
     def run_ens(idx, prec, shape, t_end):
         g, thr, jt = shape
-        ens = nb.Ensemble(sizes[idx], *cat(idx), EPS, precision=prec)
+        ens = nb.Ensemble(sizes[idx], *cat(idx), EPS, precision=prec, step_noise=args.step_noise)
         ens.set_shape(g or None, thr, jt or None)
         used = ens.shape()
         _, it0, _ = ens.stats()
@@ -817,7 +821,7 @@ def adjoint_bench(args):
     return 0
 
 
-def integrate_run(nb, np, torch, n, prec_name, t_end=1.0 / 16):
+def integrate_run(nb, np, torch, n, prec_name, t_end=1.0 / 16, step_noise=0.0):
     """Plummer N = n (equal masses, eps 1e-4, seed 2): one full-N evaluation
     (n^2 interactions), then block-step integration to t_end through
     nb_run_until (active sets from 1 to N particles), dt_max = 2^-4 so that
@@ -826,7 +830,7 @@ def integrate_run(nb, np, torch, n, prec_name, t_end=1.0 / 16):
     prec = {"mixed": nb.NB_MIXED, "fp64": nb.NB_FP64, "ex": nb.NB_EX, "sp": nb.NB_SP}[prec_name]
     m, x, v = ni.plummer(n, 2)
     stream = torch.cuda.current_stream()
-    ctx = nb.NBody(m, x, v, EPS, precision=prec, stream=stream, dt_max=2.0 ** -4)
+    ctx = nb.NBody(m, x, v, EPS, precision=prec, stream=stream, dt_max=2.0 ** -4, step_noise=step_noise)
     ctx.predict(0.0)
     ctx.evaluate(None, out=False)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -848,7 +852,8 @@ def integrate_run(nb, np, torch, n, prec_name, t_end=1.0 / 16):
     flops = FLOPS_PER_INTERACTION * float(n) * n / full_s / 1e12
     peak = PEAK_FP64_TFLOPS if prec == nb.NB_FP64 else PEAK_FP32_TFLOPS
     n_fp32_ops = {nb.NB_EX: EX_OPS_PER_INTERACTION}.get(prec)
-    return {"workload": f"plummer_N{n}_eps1e-4_{prec_name}", "full_eval_s": full_s,
+    return {"workload": f"plummer_N{n}_eps1e-4_{prec_name}" + (f"_noise{step_noise:g}" if step_noise else ""),
+            "full_eval_s": full_s,
             "full_eval_interactions_per_s": float(n) * n / full_s,
             "full_eval_frac_of_peak": (flops / peak if n_fp32_ops is None else
                                        n_fp32_ops * float(n) * n / full_s / PEAK_FP32_OPS),
@@ -871,7 +876,7 @@ def integrate_bench(args):
     torch.cuda.set_device(0)
     set_device_peaks(torch, 0)
     n = args.n if args.n != N_BODY else 65536
-    print(json.dumps(integrate_run(nb, np, torch, n, args.prec)))
+    print(json.dumps(integrate_run(nb, np, torch, n, args.prec, step_noise=args.step_noise)))
     return 0
 
 
@@ -930,13 +935,17 @@ def config_legs(nb, np, torch, local):
     the 256-system ensemble to t = 1/4 in EX (with all 256 systems also run
     one at a time) and in FP64, the differentiable N = 8192 trajectory (64
     steps, checkpoints every 8), and the N = 65536 block-step integration
-    to t = 1/16 in EX and FP64."""
+    to t = 1/16 in EX, FP64 and mixed (with the step criterion as is, and
+    with its rounding floor at 4e-7, nb_config.step_noise)."""
     legs = {}
     for name, fn in (("ensemble_ex_256", lambda: ensemble_leg(nb, np, torch, "ex")),
                      ("ensemble_fp64_256", lambda: ensemble_leg(nb, np, torch, "fp64", sample=0)),
                      ("adjoint_n8192", lambda: adjoint_run(torch)),
                      ("integrate_n65536_ex", lambda: integrate_run(nb, np, torch, 65536, "ex")),
-                     ("integrate_n65536_fp64", lambda: integrate_run(nb, np, torch, 65536, "fp64"))):
+                     ("integrate_n65536_fp64", lambda: integrate_run(nb, np, torch, 65536, "fp64")),
+                     ("integrate_n65536_mixed", lambda: integrate_run(nb, np, torch, 65536, "mixed")),
+                     ("integrate_n65536_mixed_floor4e-7",
+                      lambda: integrate_run(nb, np, torch, 65536, "mixed", step_noise=4e-7))):
         with Clocks(local) as clk:
             rec = fn()
         rec["clocks"] = clk.summary()
@@ -963,7 +972,9 @@ def precision_study(args):
     res = {"workload": f"precision_study_plummer_N{n}_equal_eps1e-4_t{args.ps_t_end:g}",
            "sample_dt": args.ps_dt, "t_end": args.ps_t_end}
     for name in args.ps_precs.split(","):
-        ctx = nb.NBody(m, x, v, EPS, precision=precs[name], dt_max=args.ps_dt)
+        base, _, noise = name.partition("@")
+        ctx = nb.NBody(m, x, v, EPS, precision=precs[base], dt_max=args.ps_dt,
+                       step_noise=float(noise) if noise else 0.0)
         t0 = time.perf_counter()
         steps, d = ctx.run_diag(args.ps_t_end, args.ps_dt)
         el = time.perf_counter() - t0

@@ -123,10 +123,21 @@ typedef struct {
                           the host-driven path, and after a launch that took
                           no step the host tries again only after 1, 3, 7 ...
                           host steps); 0: every step host-driven            */
+    double step_noise;  /* 0: the generalised Aarseth criterion as is.  > 0:
+                          the relative rounding level of the evaluated a,
+                          jerk and snap (about 4e-7 = 2^-21 for NB_MIXED,
+                          the error of m q q^2 from its two hardware
+                          estimates); the parts
+                          of the interpolated crackle, pop and a^(5) below
+                          their rounding floor (the residuals' rounding
+                          divided by h^3 .. h^5) are discounted before the
+                          criterion.  For mixed contexts and ensembles,
+                          whose FP32 rounding otherwise drives close pairs
+                          to dt_min (ensembles use it as well).  [0, 1e-3] */
 } nb_config;
 
 /* Fill cfg with the defaults listed above (FP64, automatic tiles,
- * start_forces = 1, device_steps = 1). */
+ * start_forces = 1, device_steps = 1, step_noise = 0). */
 void nb_config_default(nb_config *cfg);
 
 /* Create a context on the current CUDA device for n particles with masses

@@ -52,7 +52,7 @@ class Config(C.Structure):
     _fields_ = [("precision", C.c_int32), ("eta", C.c_double), ("eta_s", C.c_double),
                 ("dt_min", C.c_double), ("dt_max", C.c_double), ("dt_shared", C.c_double),
                 ("tiles", Tiles), ("start_forces", C.c_int32), ("stream", C.c_void_p),
-                ("device_steps", C.c_int32)]
+                ("device_steps", C.c_int32), ("step_noise", C.c_double)]
 
 
 _d = C.POINTER(C.c_double)
@@ -201,7 +201,7 @@ class NBody:
 
     def __init__(self, m, x, v, eps, precision=NB_FP64, eta=0.4, eta_s=0.01,
                  dt_min=2.0 ** -20, dt_max=2.0 ** -3, dt_shared=0.0, tiles=None, stream=None,
-                 start_forces=True, device_steps=True):
+                 start_forces=True, device_steps=True, step_noise=0.0):
         m = _f64(m)
         n = m.size
         x, v = _f64(x, (n, 3)), _f64(v, (n, 3))
@@ -214,6 +214,7 @@ class NBody:
                 setattr(cfg.tiles, k, int(val))
         cfg.start_forces = 1 if start_forces else 0
         cfg.device_steps = 1 if device_steps else 0
+        cfg.step_noise = float(step_noise)
         cfg.stream = _stream_handle(stream)
         self.n = n
         self.precision = precision
@@ -431,7 +432,7 @@ class Ensemble:
     """
 
     def __init__(self, sizes, m, x, v, eps, precision=NB_FP64, eta=0.4, eta_s=0.01,
-                 dt_min=2.0 ** -20, dt_max=2.0 ** -3, dt_shared=0.0, stream=None):
+                 dt_min=2.0 ** -20, dt_max=2.0 ** -3, dt_shared=0.0, stream=None, step_noise=0.0):
         sizes = np.ascontiguousarray(sizes, dtype=np.int64)
         m = _f64(m)
         n = m.size
@@ -441,6 +442,7 @@ class Ensemble:
         _lib.nb_config_default(C.byref(cfg))
         cfg.precision, cfg.eta, cfg.eta_s = precision, eta, eta_s
         cfg.dt_min, cfg.dt_max, cfg.dt_shared = dt_min, dt_max, dt_shared
+        cfg.step_noise = float(step_noise)
         if stream is not None:
             cfg.stream = _stream_handle(stream)
         self.sizes = sizes

@@ -26,7 +26,7 @@ struct CorrectArgs {
     int ostride;
     int n_act;
     int n;
-    double t1, eta, dt_min, dt_max, dt_shared;
+    double t1, eta, dt_min, dt_max, dt_shared, noise;
     nb_ctl *ctl;
 };
 
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(128) correct_kernel(CorrectArgs a)
     for (int q = 0; q < 9; ++q)
         f[q] = a.anew[q * (size_t)a.ostride + k];
     nbk::correct_particle_fp64(a.st, a.t, a.dt, static_cast<size_t>(a.n), a.act[k], a.t1, f, a.eta,
-                               a.dt_min, a.dt_max, a.dt_shared, a.ctl);
+                               a.dt_min, a.dt_max, a.dt_shared, a.ctl, a.noise);
 }
 
 // Start-up (nb_init): pass 0 stores a and jerk of the first evaluation (made
@@ -152,6 +152,7 @@ cudaError_t nb_launch_correct(nb_ctx *c, double t1, int n_act)
     a.n = static_cast<int>(c->n);
     a.t1 = t1;
     a.eta = c->cfg.eta;
+    a.noise = c->cfg.step_noise;
     a.dt_min = c->cfg.dt_min;
     a.dt_max = c->cfg.dt_max;
     a.dt_shared = c->cfg.dt_shared;

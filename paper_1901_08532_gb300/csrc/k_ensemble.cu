@@ -39,6 +39,7 @@
 #include <string>
 #include <vector>
 
+#include "nb_correct.cuh"
 #include "nb_device.cuh"
 #include "nb_ff.cuh"
 #include "nb_internal.cuh"
@@ -109,6 +110,7 @@ struct EnsArgs {
     int64_t *log_off;
     long long log_cap, idx_cap;
     double t_end, eps2, eta, eta_s, dt_min, dt_max, dt_shared;
+    double noise;                  // step-criterion rounding floor (nb_config.step_noise)
     int mode;  // 0: block steps to t_end, 1: start-up (a, jerk, snap, starting steps)
     int jtile;
 };
@@ -467,44 +469,13 @@ __device__ bool eval_share(const EnsArgs &a, int off, int j0, int j1, int s0, in
 }
 
 // Corrector, interpolation and new step of particle i at time tn, with its
-// new acceleration, jerk and snap f[0..8].
-__device__ void correct_one(const EnsArgs &a, int i, double tn, const double (&f)[9])
+// new acceleration, jerk and snap f[0..8]: the FP64 corrector a context uses
+// (so an ensemble takes a context's decisions), with the ensemble's
+// step-criterion noise floor (nb_config.step_noise).
+__device__ __forceinline__ void correct_one(const EnsArgs &a, int i, double tn, const double (&f)[9])
 {
-    const size_t P = static_cast<size_t>(a.P);
-    const double h = tn - a.t[i];
-    const double ih = 1.0 / h;
-    double n2[6] = {0, 0, 0, 0, 0, 0};
-    bool finite = true;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        double *px = a.st + (F_X * 3 + d) * P + i, *pv = a.st + (F_V * 3 + d) * P + i;
-        double *pa = a.st + (F_A * 3 + d) * P + i, *pj = a.st + (F_J * 3 + d) * P + i;
-        double *ps = a.st + (F_S * 3 + d) * P + i, *pc = a.st + (F_C * 3 + d) * P + i;
-        const double a1 = f[d], j1 = f[3 + d], s1v = f[6 + d];
-        const Corrected r = hermite_correct(h, ih, *px, *pv, *pa, *pj, *ps, a1, j1, s1v);
-        finite = finite && isfinite(r.x1) && isfinite(r.v1) && isfinite(r.c1);
-        *px = r.x1;
-        *pv = r.v1;
-        *pa = a1;
-        *pj = j1;
-        *ps = s1v;
-        *pc = r.c1;
-
-        n2[0] = fma(a1, a1, n2[0]);
-        n2[1] = fma(j1, j1, n2[1]);
-        n2[2] = fma(s1v, s1v, n2[2]);
-        n2[3] = fma(r.c1, r.c1, n2[3]);
-        n2[4] = fma(r.d1, r.d1, n2[4]);
-        n2[5] = fma(r.e1, r.e1, n2[5]);
-    }
-    a.t[i] = tn;
-    bool hit = false;
-    a.dt[i] = a.dt_shared > 0.0 ? a.dt_shared
-                                : quantise(aarseth_dt(n2, a.eta), a.dt[i], tn, a.dt_min, a.dt_max, &hit);
-    if (hit)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->floor_hits), 1ull);
-    if (!finite)
-        atomicOr(&a.ctl->err, NB_ERR_NONFINITE);
+    correct_particle_fp64(a.st, a.t, a.dt, static_cast<size_t>(a.P), i, tn, f, a.eta, a.dt_min, a.dt_max,
+                          a.dt_shared, a.ctl, a.noise);
 }
 
 // |v| of a 3-vector in FP32 without overflow of the squares.
@@ -530,11 +501,14 @@ __device__ void correct_one_mixed(const EnsArgs &a, int i, double tn, const doub
     const float h = __double2float_rn(tn - a.t[i]);
     const float ih = 1.0f / h;
     const float ih3 = ih * ih * ih;
-    float an[3], jn[3], sn[3], cn[3], dn[3], en[3];
+    float an[3], jn[3], sn[3], cn[3], dn[3], en[3], ao[3], jo[3], so[3];
     bool finite = true;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const float a0 = a.st32[(3 + d) * P + i], j0 = a.st32[(6 + d) * P + i], s0 = a.st32[(9 + d) * P + i];
+        ao[d] = a0;
+        jo[d] = j0;
+        so[d] = s0;
         const float a1 = __double2float_rn(f[d]), j1 = __double2float_rn(f[3 + d]);
         const float s1 = __double2float_rn(f[6 + d]);
         const float v0f = a.st32[d * P + i];
@@ -574,11 +548,26 @@ __device__ void correct_one_mixed(const EnsArgs &a, int i, double tn, const doub
     if (a.dt_shared > 0.0) {
         a.dt[i] = a.dt_shared;
     } else {
-        // generalised Aarseth criterion eta (A1 / A4)^(1/3)
-        const float A1 = sqrtf(norm3f(an[0], an[1], an[2])) * sqrtf(norm3f(sn[0], sn[1], sn[2])) +
-                         norm3f(jn[0], jn[1], jn[2]);
-        const float A4 = sqrtf(norm3f(cn[0], cn[1], cn[2])) * sqrtf(norm3f(en[0], en[1], en[2])) +
-                         norm3f(dn[0], dn[1], dn[2]);
+        // generalised Aarseth criterion eta (A1 / A4)^(1/3); with a noise
+        // level, crackle, pop and a^(5) less their rounding floors (as in
+        // correct_particle_fp64)
+        const float na1 = norm3f(an[0], an[1], an[2]), nj1 = norm3f(jn[0], jn[1], jn[2]);
+        const float ns1 = norm3f(sn[0], sn[1], sn[2]);
+        float nc = norm3f(cn[0], cn[1], cn[2]), nd = norm3f(dn[0], dn[1], dn[2]);
+        float ne = norm3f(en[0], en[1], en[2]);
+        if (a.noise > 0.0) {
+            const float z = static_cast<float>(a.noise);
+            const float o_a = norm3f(ao[0], ao[1], ao[2]), o_j = norm3f(jo[0], jo[1], jo[2]);
+            const float o_s = norm3f(so[0], so[1], so[2]);
+            const float s1f = z * (na1 + o_a + h * (o_j + 0.5f * h * o_s));
+            const float s2f = z * h * (nj1 + o_j + h * o_s);
+            const float s3f = z * h * h * (ns1 + o_s);
+            nc = fmaxf(nc - (60.0f * s1f + 36.0f * s2f + 9.0f * s3f) * ih3, 0.0f);
+            nd = fmaxf(nd - (360.0f * s1f + 192.0f * s2f + 36.0f * s3f) * ih3 * ih, 0.0f);
+            ne = fmaxf(ne - (720.0f * s1f + 360.0f * s2f + 60.0f * s3f) * ih3 * ih * ih, 0.0f);
+        }
+        const float A1 = sqrtf(na1) * sqrtf(ns1) + nj1;
+        const float A4 = sqrtf(nc) * sqrtf(ne) + nd;
         // A1 = A4 = 0: no force, no bound (dt_max), as in aarseth_dt()
         const float crit = (A1 == 0.0f && A4 == 0.0f) ? INFINITY : static_cast<float>(a.eta) * cbrtf(A1 / A4);
         a.dt[i] = quantise(static_cast<double>(crit), a.dt[i], tn, a.dt_min, a.dt_max, &hit);
@@ -1312,6 +1301,7 @@ EnsArgs make_args(nb_ensemble *e, int mode, double t_end)
     a.t_end = t_end;
     a.eps2 = e->eps * e->eps;
     a.eta = e->cfg.eta;
+    a.noise = e->cfg.step_noise;
     a.eta_s = e->cfg.eta_s;
     a.dt_min = e->cfg.dt_min;
     a.dt_max = e->cfg.dt_max;
@@ -1446,7 +1436,7 @@ nb_status nb_ensemble_init(nb_ensemble **out, int32_t n_systems, const int64_t *
          cf.precision != NB_MIXED32) || !(cf.eta > 0) ||
         !(cf.eta_s > 0) ||
         !pow2(cf.dt_min) || !pow2(cf.dt_max) || cf.dt_min > cf.dt_max ||
-        (cf.dt_shared != 0.0 && !pow2(cf.dt_shared))) {
+        (cf.dt_shared != 0.0 && !pow2(cf.dt_shared)) || !(cf.step_noise >= 0.0) || !(cf.step_noise <= 1e-3)) {
         nb_set_thread_error("invalid configuration");
         return NB_EINVAL;
     }

@@ -54,7 +54,7 @@ struct StepArgs {
     int n;
     double *st, *t, *dt;
     const double *m;
-    double eps2, eta, dt_min, dt_max, dt_shared, t_end;
+    double eps2, eta, dt_min, dt_max, dt_shared, t_end, noise;
     int drop_lo;        // single-precision control: positions without their low part
     double *bmin;       // [B] per-block earliest t_i + dt_i
     int *bcnt;          // [B] particles reaching it
@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a)
                 for (int q = 0; q < 9; ++q)
                     f[q] = s_f[k][q];
                 correct_particle_fp64(a.st, a.t, a.dt, static_cast<size_t>(a.n), i, mn, f, a.eta, a.dt_min,
-                                      a.dt_max, a.dt_shared, a.ctl);
+                                      a.dt_max, a.dt_shared, a.ctl, a.noise);
             }
         if (bk == 0) {
             for (int k = tid; k < total; k += T)
@@ -566,6 +566,7 @@ cudaError_t nb_run_stepper(nb_ctx *c, double t_end, int64_t log_cap, int64_t log
     a.m = c->m;
     a.eps2 = c->eps * c->eps;
     a.eta = c->cfg.eta;
+    a.noise = c->cfg.step_noise;
     a.dt_min = c->cfg.dt_min;
     a.dt_max = c->cfg.dt_max;
     a.dt_shared = c->cfg.dt_shared;

@@ -70,6 +70,8 @@ std::string check_config(const nb_config &c)
         return "dt_min and dt_max must be powers of two with dt_min <= dt_max";
     if (c.dt_shared != 0.0 && !is_pow2_double(c.dt_shared))
         return "dt_shared must be 0 or a power of two";
+    if (!(c.step_noise >= 0.0) || !(c.step_noise <= 1e-3))
+        return "step_noise must be in [0, 1e-3]";
     const nb_tiles &t = c.tiles;
     if (t.ki < 0 || t.threads < 0 || t.jtile < 0 || t.lanes < 0 || t.split < 0 || t.junroll < 0)
         return "tile fields must be >= 0";
@@ -311,6 +313,7 @@ void nb_config_default(nb_config *cfg)
     cfg->start_forces = 1;
     cfg->stream = nullptr;
     cfg->device_steps = 1;
+    cfg->step_noise = 0.0;
 }
 
 nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x, const double *v,

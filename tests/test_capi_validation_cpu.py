@@ -34,6 +34,7 @@ def test_config_defaults():
     assert cfg.precision == nb.NB_FP64 and cfg.eta == 0.4 and cfg.eta_s == 0.01
     assert cfg.dt_min == 2.0 ** -20 and cfg.dt_max == 2.0 ** -3 and cfg.dt_shared == 0.0
     assert cfg.start_forces == 1 and cfg.device_steps == 1 and not cfg.stream
+    assert cfg.step_noise == 0.0
 
 
 @pytest.mark.parametrize("kw, msg", [
@@ -48,6 +49,8 @@ def test_config_defaults():
     ({"dt_min": 2.0 ** -2, "dt_max": 2.0 ** -3}, "dt_min"),
     ({"dt_max": 0.1}, "powers of two"),
     ({"dt_shared": 0.3}, "dt_shared"),
+    ({"step_noise": -1e-7}, "step_noise"),
+    ({"step_noise": 0.01}, "step_noise"),
 ])
 def test_invalid_arguments_are_rejected_before_any_cuda_call(kw, msg):
     st, ctx, err = _init(**kw)

@@ -68,8 +68,8 @@ def test_fp64_ensemble_launch_shapes_agree():
         np.testing.assert_array_equal(st["t"], out[0]["t"])
 
 
-@pytest.mark.parametrize("prec, tol_xv", [(1, 1e-8), (4, 1e-7)])
-def test_mixed_ensembles_match_oracle_replay_per_system(prec, tol_xv):
+@pytest.mark.parametrize("prec, tol_xv, noise", [(1, 1e-8, 0.0), (4, 1e-7, 0.0), (1, 1e-8, 4e-7)])
+def test_mixed_ensembles_match_oracle_replay_per_system(prec, tol_xv, noise):
     """Mixed ensembles against the FP64 oracle, system by system.  FP32 pair
     arithmetic may move a step decision across a power of two (another valid
     trajectory), so the oracle replays each system's logged (t_next, active
@@ -90,12 +90,14 @@ def test_mixed_ensembles_match_oracle_replay_per_system(prec, tol_xv):
     x and v; NB_MIXED32 (4) forms the corrector's increments in FP32 (about
     6e-8 of each increment): 1e-7.  The run is short (to t = 2^-10, block
     steps down to 2^-20), since the per-step force rounding of a few 1e-8
-    grows along close encounters."""
+    grows along close encounters.  With a step-criterion noise floor
+    (nb_config.step_noise) the decisions change, and the replay checks
+    the same arithmetic along them."""
     nb = nb_gpu()
     sizes = [2, 5, 16, 33, 300, 64, 257]
     ms, xs, vs = _systems(sizes, 110)
     eps, t_end = 1e-4, 2.0 ** -10
-    ens = nb.Ensemble(sizes, *_concat(ms, xs, vs), eps, precision=prec, dt_max=t_end)
+    ens = nb.Ensemble(sizes, *_concat(ms, xs, vs), eps, precision=prec, dt_max=t_end, step_noise=noise)
     ens.set_log(1 << 20, 1 << 24)
     ens.run(t_end)
     st = ens.state()

@@ -880,7 +880,7 @@ def integrate_bench(args):
     return 0
 
 
-def ensemble_leg(nb, np, torch, prec_name="ex", t_end=0.25, sample=256):
+def ensemble_leg(nb, np, torch, prec_name="ex", t_end=0.25, sample=256, step_noise=0.0):
     """Batched ensemble (256 Plummer systems, N log-uniform in [256, 16384],
     seed 4, eps 1e-4, own block steps) to t_end in one persistent
     graph-captured launch at the library's default shape, then `sample`
@@ -893,7 +893,7 @@ def ensemble_leg(nb, np, torch, prec_name="ex", t_end=0.25, sample=256):
 
     def run(idx):
         cat = [np.concatenate([parts[k][f] for k in idx]) for f in range(3)]
-        ens = nb.Ensemble(sizes[idx], *cat, EPS, precision=prec)
+        ens = nb.Ensemble(sizes[idx], *cat, EPS, precision=prec, step_noise=step_noise)
         _, it0, _ = ens.stats()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -905,7 +905,8 @@ def ensemble_leg(nb, np, torch, prec_name="ex", t_end=0.25, sample=256):
         return {"seconds": el, "interactions": it1 - it0, "interactions_per_s": (it1 - it0) / el,
                 "block_steps": int(steps.sum()), "shape": list(shape)}
 
-    out = {"workload": f"ensemble_256_plummer_N256-16384_eps1e-4_{prec_name}_t{t_end:g}",
+    out = {"workload": f"ensemble_256_plummer_N256-16384_eps1e-4_{prec_name}_t{t_end:g}"
+                       + (f"_floor{step_noise:g}" if step_noise else ""),
            "systems": int(sizes.size), "particles": int(sizes.sum()), "all": run(list(range(sizes.size)))}
     if sample <= 0:
         return out
@@ -933,13 +934,16 @@ def ensemble_leg(nb, np, torch, prec_name="ex", t_end=0.25, sample=256):
 def config_legs(nb, np, torch, local):
     """The other configurations, compact, each under its own clock record:
     the 256-system ensemble to t = 1/4 in EX (with all 256 systems also run
-    one at a time) and in FP64, the differentiable N = 8192 trajectory (64
+    one at a time), in FP64, and in mixed with the step criterion's rounding
+    floor at 4e-7 (nb_config.step_noise), the differentiable N = 8192 trajectory (64
     steps, checkpoints every 8), and the N = 65536 block-step integration
     to t = 1/16 in EX, FP64 and mixed (with the step criterion as is, and
     with its rounding floor at 4e-7, nb_config.step_noise)."""
     legs = {}
     for name, fn in (("ensemble_ex_256", lambda: ensemble_leg(nb, np, torch, "ex")),
                      ("ensemble_fp64_256", lambda: ensemble_leg(nb, np, torch, "fp64", sample=0)),
+                     ("ensemble_mixed_256_floor4e-7",
+                      lambda: ensemble_leg(nb, np, torch, "mixed", sample=0, step_noise=4e-7)),
                      ("adjoint_n8192", lambda: adjoint_run(torch)),
                      ("integrate_n65536_ex", lambda: integrate_run(nb, np, torch, 65536, "ex")),
                      ("integrate_n65536_fp64", lambda: integrate_run(nb, np, torch, 65536, "fp64")),

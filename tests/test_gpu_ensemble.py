@@ -212,3 +212,46 @@ def test_lone_particle_system_coasts_at_the_largest_step(prec):
     np.testing.assert_array_equal(st["v"][0], v1[0])
     assert st["dt"][0] == 0.125 and st["t"][0] == 0.25
     assert np.isfinite(st["x"]).all() and (st["t"] == 0.25).all()
+
+
+def test_full_size_ensemble_sampled_systems_match_oracle():
+    """The 256-system ensemble at full size (N log-uniform in [256, 16384],
+    1,004,043 particles, seeds as in the bench, eps = 1e-4) in EX at the
+    library's default launch shape, to t = 1/4 in one persistent launch,
+    with the step log on.  Sampled systems (the three smallest and those
+    nearest 1000 and 2000 particles, so both the small-set and the large-set
+    evaluation paths run): the oracle, run on its own, takes the same block
+    steps (every logged time and active set), and ends on the same t and dt
+    exactly and on x, v to 1e-10 (EX sums are within about 1e-13 of the FP64
+    sums)."""
+    nb = nb_gpu()
+    eps, t_end = 1e-4, 0.25
+    sizes = ni.ensemble_sizes(256, 4)
+    parts = [ni.plummer(int(k), 1000 + q) for q, k in enumerate(sizes)]
+    ens = nb.Ensemble(sizes, *[np.concatenate([p[f] for p in parts]) for f in range(3)], eps,
+                      precision=nb.NB_EX)
+    ens.set_log(1 << 20, 1 << 28)
+    ens.run(t_end)
+    st = ens.state()
+    steps, _, _ = ens.stats()
+    log, (n_steps, n_idx) = ens.log()
+    ens.close()
+    assert n_steps == int(steps.sum()) and n_idx <= 1 << 28
+    order = np.argsort(sizes)
+    pick = [int(order[0]), int(order[1]), int(order[2]), int(np.argmin(np.abs(sizes - 1000))),
+            int(np.argmin(np.abs(sizes - 2000)))]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    for k in pick:
+        sl = slice(int(offs[k]), int(offs[k + 1]))
+        ref = O.System(*parts[k], eps)
+        nsteps, (lt, ln, lh) = ref.run_until(t_end, log_cap=int(steps[k]) + 16)
+        sr = ref.state()
+        assert steps[k] == nsteps and len(log[k]) == nsteps, (k, steps[k], nsteps)
+        assert all(idx is not None for _, idx in log[k])
+        np.testing.assert_array_equal([t for t, _ in log[k]], lt)
+        np.testing.assert_array_equal([len(idx) for _, idx in log[k]], ln)
+        assert [O.set_hash(idx) for _, idx in log[k]] == [int(h) for h in lh], k
+        np.testing.assert_array_equal(st["t"][sl], sr["t"])
+        np.testing.assert_array_equal(st["dt"][sl], sr["dt"])
+        for f in ("x", "v"):
+            assert rel_err(st[f][sl], sr[f]).max() < 1e-10, (k, f, rel_err(st[f][sl], sr[f]).max())

@@ -52,7 +52,7 @@ def build(force: bool = False) -> str:
 
 class orc_params(C.Structure):
     _fields_ = [("eta", C.c_double), ("eta_s", C.c_double), ("dt_min", C.c_double),
-                ("dt_max", C.c_double), ("dt_shared", C.c_double)]
+                ("dt_max", C.c_double), ("dt_shared", C.c_double), ("step_noise", C.c_double)]
 
 
 def lib():
@@ -70,6 +70,9 @@ def lib():
             L.orc_interpolate.argtypes = [C.c_double] + [_d] * 9
             L.orc_dt_crit.argtypes = [C.c_double] + [_d] * 6
             L.orc_dt_crit.restype = C.c_double
+            L.orc_interp_floor.argtypes = [C.c_double, C.c_double] + [_d] * 7
+            L.orc_dt_crit_floored.argtypes = [C.c_double] + [_d] * 7
+            L.orc_dt_crit_floored.restype = C.c_double
             L.orc_dt_initial.argtypes = [C.c_double, _d, _d, _d]
             L.orc_dt_initial.restype = C.c_double
             L.orc_dt_quantise.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_int)]
@@ -170,6 +173,18 @@ def dt_crit(eta, a, j, s, c, d, e):
     return lib().orc_dt_crit(float(eta), *[_p(_f(q, 3)) for q in (a, j, s, c, d, e)])
 
 
+def interp_floor(noise, h, a0, j0, s0, a1, j1, s1):
+    """Rounding floors (of |c1|, |d1|, |e1|) for inputs with relative error `noise`."""
+    out = np.zeros(3)
+    lib().orc_interp_floor(float(noise), float(h), *[_p(_f(q, 3)) for q in (a0, j0, s0, a1, j1, s1)],
+                           _p(out))
+    return out
+
+
+def dt_crit_floored(eta, a, j, s, c, d, e, floor):
+    return lib().orc_dt_crit_floored(float(eta), *[_p(_f(q, 3)) for q in (a, j, s, c, d, e, floor)])
+
+
 def dt_initial(eta_s, a, j, s):
     return lib().orc_dt_initial(float(eta_s), *[_p(_f(q, 3)) for q in (a, j, s)])
 
@@ -217,10 +232,10 @@ class System:
     """The whole integrator: block (or shared) time steps from t = 0."""
 
     def __init__(self, m, x, v, eps, eta=0.4, eta_s=0.01, dt_min=2.0 ** -20,
-                 dt_max=2.0 ** -3, dt_shared=0.0):
+                 dt_max=2.0 ** -3, dt_shared=0.0, step_noise=0.0):
         m = _f(m)
         self.n = m.size
-        self.params = orc_params(eta, eta_s, dt_min, dt_max, dt_shared)
+        self.params = orc_params(eta, eta_s, dt_min, dt_max, dt_shared, step_noise)
         self._h = lib().orc_create(self.n, _p(m), _p(_f(x, (self.n, 3))),
                                    _p(_f(v, (self.n, 3))), float(eps), C.byref(self.params))
         if not self._h:

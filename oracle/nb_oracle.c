@@ -254,6 +254,66 @@ double orc_dt_crit(double eta, const double a[3], const double j[3],
     return eta * cbrt(A1 / A4);
 }
 
+/* Rounding floors of the interpolated crackle, pop and a^(5), for the step
+ * criterion read under rounding (section 3 item 3's criterion assumes those
+ * derivatives are resolved).  Each input a0, j0, s0, a1, j1, s1 is taken to
+ * carry an error of at most `noise` times its norm.  The three residuals of
+ * the interpolation's system (orc_interpolate) are linear in the inputs, so
+ * each residual's error is at most noise times the sum of |coefficient| x
+ * |input| over its own terms:
+ *   rho_1 = noise (|a1| + |a0| + h |j0| + h^2/2 |s0|)    (a1 - a0 - j0 h - s0 h^2/2)
+ *   rho_2 = noise h (|j1| + |j0| + h |s0|)               (h (j1 - j0 - s0 h))
+ *   rho_3 = noise h^2 (|s1| + |s0|)                      (h^2 (s1 - s0))
+ * The end-of-step derivatives are linear in the residuals, (c1 h^3, d1 h^4,
+ * e1 h^5) = G (R1, R2, R3); taking each residual's error as independent,
+ * floor_q = sum_k |G_qk| rho_k / h^(3+q).  G is formed here column by
+ * column, as the interpolation's response to a unit residual, by the same
+ * elimination as orc_interpolate. */
+void orc_interp_floor(double noise, double h, const double a0[3], const double j0[3],
+                      const double s0[3], const double a1[3], const double j1[3],
+                      const double s1[3], double floor[3])
+{
+    double rho[3];
+    rho[0] = noise * (norm3(a1) + norm3(a0) + h * norm3(j0) + h * h / 2.0 * norm3(s0));
+    rho[1] = noise * h * (norm3(j1) + norm3(j0) + h * norm3(s0));
+    rho[2] = noise * h * h * (norm3(s1) + norm3(s0));
+    double G[3][3];
+    for (int k = 0; k < 3; k++) {
+        double M[3][3] = {{1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0},
+                          {1.0 / 2.0, 1.0 / 6.0, 1.0 / 24.0},
+                          {1.0, 1.0 / 2.0, 1.0 / 6.0}};
+        double r[3] = {0.0, 0.0, 0.0};
+        r[k] = 1.0;
+        double y[3];
+        solve3(M, r, y);
+        G[0][k] = y[0] + y[1] + y[2] / 2.0;
+        G[1][k] = y[1] + y[2];
+        G[2][k] = y[2];
+    }
+    double hk = h * h * h;
+    for (int q = 0; q < 3; q++) {
+        floor[q] = (fabs(G[q][0]) * rho[0] + fabs(G[q][1]) * rho[1] + fabs(G[q][2]) * rho[2]) / hk;
+        hk *= h;
+    }
+}
+
+/* The criterion of orc_dt_crit with |c|, |d|, |e| replaced by the parts
+ * above their rounding floors, max(|c| - floor[0], 0) and so on: only
+ * resolved derivatives bound the step. */
+double orc_dt_crit_floored(double eta, const double a[3], const double j[3],
+                           const double s[3], const double c[3], const double d[3],
+                           const double e[3], const double floor[3])
+{
+    double nc = fmax(norm3(c) - floor[0], 0.0);
+    double nd = fmax(norm3(d) - floor[1], 0.0);
+    double ne = fmax(norm3(e) - floor[2], 0.0);
+    double A1 = sqrt(norm3(a) * norm3(s)) + norm3(j);
+    double A4 = sqrt(nc * ne) + nd;
+    if (A1 == 0.0 && A4 == 0.0)
+        return INFINITY;
+    return eta * cbrt(A1 / A4);
+}
+
 double orc_dt_initial(double eta_s, const double a[3], const double j[3],
                       const double s[3])
 {
@@ -413,6 +473,10 @@ static void advance_active(orc_sys *s, double tn, int64_t n_act, int keep_dt)
                     &s->s[3 * i], &s->a1[3 * k], &s->j1[3 * k], &s->s1[3 * k], x1, v1);
         orc_interpolate(h, &s->a[3 * i], &s->j[3 * i], &s->s[3 * i], &s->a1[3 * k],
                         &s->j1[3 * k], &s->s1[3 * k], c1, d1, e1);
+        double fl[3] = {0.0, 0.0, 0.0};
+        if (s->p.step_noise > 0.0)
+            orc_interp_floor(s->p.step_noise, h, &s->a[3 * i], &s->j[3 * i], &s->s[3 * i],
+                             &s->a1[3 * k], &s->j1[3 * k], &s->s1[3 * k], fl);
         for (int q = 0; q < 3; q++) {
             s->x[3 * i + q] = x1[q];
             s->v[3 * i + q] = v1[q];
@@ -428,8 +492,11 @@ static void advance_active(orc_sys *s, double tn, int64_t n_act, int keep_dt)
             s->dt[i] = s->p.dt_shared;
         } else {
             int hit = 0;
-            double crit = orc_dt_crit(s->p.eta, &s->a[3 * i], &s->j[3 * i],
-                                      &s->s[3 * i], c1, d1, e1);
+            double crit = s->p.step_noise > 0.0
+                              ? orc_dt_crit_floored(s->p.eta, &s->a[3 * i], &s->j[3 * i],
+                                                    &s->s[3 * i], c1, d1, e1, fl)
+                              : orc_dt_crit(s->p.eta, &s->a[3 * i], &s->j[3 * i],
+                                            &s->s[3 * i], c1, d1, e1);
             s->dt[i] = orc_dt_quantise(crit, s->dt[i], tn, s->p.dt_min, s->p.dt_max, &hit);
             s->floor_hits += hit;
         }

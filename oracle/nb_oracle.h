@@ -67,6 +67,20 @@ double orc_dt_crit(double eta, const double a[3], const double j[3],
                    const double s[3], const double c[3], const double d[3],
                    const double e[3]);
 
+/* Rounding floors of the interpolated crackle, pop and a^(5) when every
+ * input vector carries a relative error up to `noise`: the residuals'
+ * error bounds rho_1..rho_3 (noise times the sum of |coefficient| x |input|
+ * of each residual) propagated through the absolute values of the
+ * interpolation's linear map; floor[0..2] for |c1|, |d1|, |e1|. */
+void orc_interp_floor(double noise, double h, const double a0[3], const double j0[3],
+                      const double s0[3], const double a1[3], const double j1[3],
+                      const double s1[3], double floor[3]);
+
+/* orc_dt_crit with |c|, |d|, |e| less their floors (at least 0). */
+double orc_dt_crit_floored(double eta, const double a[3], const double j[3],
+                           const double s[3], const double c[3], const double d[3],
+                           const double e[3], const double floor[3]);
+
 /* Starting step before any interpolation exists:
  * eta_s * min(|a|/|j|, sqrt(|a|/|s|)), a ratio 0/0 counting as no bound. */
 double orc_dt_initial(double eta_s, const double a[3], const double j[3],
@@ -100,6 +114,8 @@ typedef struct {
     double dt_min;   /* smallest allowed block step               */
     double dt_max;   /* largest allowed block step                */
     double dt_shared;/* > 0: every particle steps with this dt    */
+    double step_noise;/* > 0: criterion with rounding floors of    */
+                      /* this relative level (orc_interp_floor)    */
 } orc_params;
 
 /* Copies m, x, v; evaluates a, j (pass 1, a_j = 0) then s (pass 2, with

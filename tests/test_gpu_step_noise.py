@@ -71,10 +71,10 @@ def test_criterion_discounts_only_the_rounding_floor(noise):
     a1, j1, s1 follow a0, j0, s0 exactly, except for a relative error of
     1e-6 planted in a1, loaded through nb_set_forces.  The quintic's
     crackle, pop and a^(5) are then that error divided by h^3, h^4, h^5,
-    and the criterion as is halves the step (the oracle's interpolation and
-    criterion give the same step); with a rounding floor of 2e-6, above the
-    planted error, they are discounted to zero, so the step stays h (it may
-    not double at a time that is not a multiple of 2h)."""
+    and the criterion as is halves the step; with a rounding floor of 2e-6,
+    above the planted error, they are discounted to zero, so the step stays
+    h (it may not double at a time that is not a multiple of 2h).  The
+    oracle's interpolation, floors and criterion give the same step."""
     nb = nb_gpu()
     import oracle as O
     h = 2.0 ** -10
@@ -96,9 +96,56 @@ def test_criterion_discounts_only_the_rounding_floor(noise):
     dt = g.state()["dt"][0]
     g.close()
     c, d, e = O.interpolate(h, a0, j0, s0, a1, j1, s1)
-    ref, _ = O.dt_quantise(O.dt_crit(0.4, a1, j1, s1, c, d, e), h, h, dt_max=2.0 ** -3)
-    if noise == 0.0:
-        assert ref == h / 2      # the planted error alone halves the step
-        assert dt == ref
+    fl = O.interp_floor(noise, h, a0, j0, s0, a1, j1, s1)
+    ref, _ = O.dt_quantise(O.dt_crit_floored(0.4, a1, j1, s1, c, d, e, fl), h, h, dt_max=2.0 ** -3)
+    assert dt == ref
+    # the planted error alone halves the step; the floor above it keeps h
+    assert ref == (h / 2 if noise == 0.0 else h)
+
+
+@pytest.mark.parametrize("case", ["plummer_1024", "close_pair_1438"])
+def test_fp64_with_rounding_floor_takes_the_oracles_decisions(case):
+    """FP64 arithmetic with the floor at 4e-7 on both sides (the oracle's
+    orc_interp_floor and floored criterion): the GPU takes the oracle's block
+    steps (time, active count and active set at every step) and ends on its
+    state to 1e-10: Plummer N = 1024 to t = 1/8, and the close-pair system
+    to t = 1/16; host-driven steps and nb_run_until alike."""
+    nb = nb_gpu()
+    import oracle as O
+    if case == "plummer_1024":
+        (m, x, v), t_end = ni.plummer(1024, 1), 0.125
     else:
-        assert dt == h
+        (m, x, v), t_end = _close_pair_system(), 2.0 ** -4
+    ref = O.System(m, x, v, 1e-4, dt_max=t_end, step_noise=4e-7)
+    steps_r, (lt_r, ln_r, lh_r) = ref.run_until(t_end, log_cap=1 << 17)
+    g = nb.NBody(m, x, v, 1e-4, dt_max=t_end, step_noise=4e-7)
+    tn, sets = [], []
+    while True:
+        t, n_act = g.step()
+        tn.append(t)
+        sets.append(g.active().copy())
+        assert sets[-1].size == n_act
+        if t == t_end and n_act == m.size:
+            break
+        assert len(tn) <= steps_r
+    st_g = g.state()
+    g.close()
+    st_r = ref.state()
+    assert len(tn) == steps_r
+    np.testing.assert_array_equal(tn, lt_r)
+    np.testing.assert_array_equal([q.size for q in sets], ln_r)
+    assert [O.set_hash(q) for q in sets] == [int(h) for h in lh_r]
+    np.testing.assert_array_equal(st_g["t"], st_r["t"])
+    np.testing.assert_array_equal(st_g["dt"], st_r["dt"])
+    for f in ("x", "v"):
+        assert np.abs(st_g[f] - st_r[f]).max() <= 1e-10 * np.abs(st_r[f]).max(), f
+    # the same run through nb_run_until (small active sets on the
+    # device-resident stepper) takes the same steps
+    g = nb.NBody(m, x, v, 1e-4, dt_max=t_end, step_noise=4e-7)
+    steps_d, (lt_d, ln_d) = g.run_until(t_end, log_cap=1 << 17)
+    st_d = g.state()
+    g.close()
+    assert steps_d == steps_r
+    np.testing.assert_array_equal(lt_d, lt_r)
+    np.testing.assert_array_equal(ln_d, ln_r)
+    np.testing.assert_array_equal(st_d["dt"], st_r["dt"])

@@ -26,7 +26,15 @@ MUTANTS = {
     "potential_unsoftened": ("m[j] / sqrt(dot3(r, r) + eps * eps));", "m[j] / sqrt(dot3(r, r)));"),
     "softening_not_squared": ("double R = dot3(r, r) + eps * eps;", "double R = dot3(r, r) + eps;"),
     "angmom_z_sign": ("r[0] * u[1] - r[1] * u[0]};", "r[1] * u[0] - r[0] * u[1]};"),
-    "no_force_floor": ("    if (A1 == 0.0 && A4 == 0.0)\n        return INFINITY;\n", ""),
+    "no_force_floor": ("norm3(d);\n    if (A1 == 0.0 && A4 == 0.0)\n        return INFINITY;\n", "norm3(d);\n"),
+    "floor_rho1_drops_j0": ("norm3(a0) + h * norm3(j0) + h * h / 2.0 * norm3(s0));",
+                            "norm3(a0) + h * h / 2.0 * norm3(s0));"),
+    "floor_rho2_power_of_h": ("rho[1] = noise * h * (norm3(j1)", "rho[1] = noise * (norm3(j1)"),
+    "floor_rho3_drops_s0": ("rho[2] = noise * h * h * (norm3(s1) + norm3(s0));",
+                            "rho[2] = noise * h * h * norm3(s1);"),
+    "floor_signed_map": ("fabs(G[q][1]) * rho[1]", "G[q][1] * rho[1]"),
+    "floor_map_crackle": ("G[0][k] = y[0] + y[1] + y[2] / 2.0;", "G[0][k] = y[0] + y[1] + y[2];"),
+    "floored_norm_sign": ("double nd = fmax(norm3(d) - floor[1], 0.0);", "double nd = fmax(norm3(d) + floor[1], 0.0);"),
 }
 PIN_FILES = ("test_oracle_pins.py", "test_golden_cpu.py")
 

@@ -444,3 +444,157 @@ def test_replay_of_own_log_reproduces_state():
     sa, sb = a.state(), b.state()
     for k in ("x", "v", "a", "j", "s", "c", "t"):
         np.testing.assert_array_equal(sa[k], sb[k])
+
+
+# ------------------------------------- step criterion with rounding floors
+#
+# The floors (orc_interp_floor) bound how far the interpolated crackle, pop
+# and a^(5) move when each input vector carries a relative error up to
+# `noise`.  They are pinned here against the interpolation itself, which is
+# pinned above (exact on quintics): its response to single inputs gives the
+# linear maps the floors must reproduce.
+
+_SLOTS = ("a0", "j0", "s0", "a1", "j1", "s1")
+
+
+def _responses(h):
+    """Per input slot, the interpolation's response (c1, d1, e1) to that
+    input alone set to the unit vector along x: a [6][3] array."""
+    out = np.zeros((6, 3))
+    for k in range(6):
+        ins = [np.zeros(3) for _ in range(6)]
+        ins[k][0] = 1.0
+        c, d, e = O.interpolate(h, *ins)
+        out[k] = c[0], d[0], e[0]
+    return out
+
+
+def _rand_inputs(rng, scale=1.0):
+    return [rng.normal(size=3) * scale * 10.0 ** rng.uniform(-3, 3) for _ in range(6)]
+
+
+def test_floor_is_zero_without_noise_and_the_criterion_reduces():
+    rng = np.random.default_rng(61)
+    for _ in range(200):
+        h = 2.0 ** -int(rng.integers(3, 21))
+        ins = _rand_inputs(rng)
+        fl = O.interp_floor(0.0, h, *ins)
+        assert np.all(fl == 0.0)
+        a, j, s, c, d, e = _rand_inputs(rng)
+        assert O.dt_crit_floored(0.4, a, j, s, c, d, e, fl) == O.dt_crit(0.4, a, j, s, c, d, e)
+
+
+@pytest.mark.parametrize("h", [2.0 ** -3, 2.0 ** -11, 2.0 ** -20])
+def test_floor_is_tight_for_inputs_of_one_residual(h):
+    """a0 and a1 enter only the first residual, j1 only the second, s1 only
+    the third: with that input alone, of norm L, the worst error (noise L
+    along the input) moves (c1, d1, e1) by exactly the floors."""
+    resp = _responses(h)
+    rng = np.random.default_rng(62)
+    noise = 4e-7
+    for slot in (0, 3, 4, 5):
+        for L in (1e-3, 1.0, 7.5e4):
+            u = rng.normal(size=3)
+            ins = [np.zeros(3) for _ in range(6)]
+            ins[slot] = L * u / np.linalg.norm(u)
+            fl = O.interp_floor(noise, h, *ins)
+            np.testing.assert_allclose(fl, np.abs(resp[slot]) * noise * L, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("h", [2.0 ** -3, 2.0 ** -11, 2.0 ** -20])
+def test_floor_propagates_independent_residual_bounds(h):
+    """Every input, alone: its coefficients in the three residuals follow
+    from the interpolation (its response solved against the responses to the
+    residuals alone, i.e. to a1, j1 / h, s1 / h^2), each residual's error is
+    bounded by noise times |coefficient| times the input's norm, and the
+    floors are those bounds through the absolute values of the map from
+    residuals to (c1, d1, e1).  Over several inputs at once the floors add."""
+    resp = _responses(h)
+    G = np.stack([resp[3], resp[4] / h, resp[5] / (h * h)], axis=1)   # [3 outputs][3 residuals]
+    noise = 1e-6
+    rng = np.random.default_rng(63)
+    total = np.zeros(3)
+    ins_all = [np.zeros(3) for _ in range(6)]
+    for slot in range(6):
+        coef = np.linalg.solve(G, resp[slot])
+        L = 10.0 ** rng.uniform(-2, 2)
+        ins = [np.zeros(3) for _ in range(6)]
+        ins[slot] = L * rng.normal(size=3)
+        ins[slot] *= L / np.linalg.norm(ins[slot])
+        ins_all[slot] = ins[slot]
+        want = np.abs(G) @ (noise * np.abs(coef) * L)
+        fl = O.interp_floor(noise, h, *ins)
+        np.testing.assert_allclose(fl, want, rtol=1e-10, atol=0)
+        total += fl
+    np.testing.assert_allclose(O.interp_floor(noise, h, *ins_all), total, rtol=1e-12, atol=0)
+
+
+def test_floor_bounds_every_perturbation_within_the_noise():
+    """Random inputs, each input vector moved by a random vector of norm up
+    to noise times its own: the interpolated derivatives move by no more
+    than the floors (vector norms), and aligned moves come close to them."""
+    rng = np.random.default_rng(64)
+    noise = 1e-6
+    worst = 0.0
+    for _ in range(400):
+        h = 2.0 ** -int(rng.integers(3, 21))
+        ins = _rand_inputs(rng)
+        pert = []
+        for q in ins:
+            dq = rng.normal(size=3)
+            pert.append(q + dq / np.linalg.norm(dq) * noise * np.linalg.norm(q) * rng.uniform())
+        fl = O.interp_floor(noise, h, *pert)
+        base = O.interpolate(h, *ins)
+        moved = O.interpolate(h, *pert)
+        for b, m_, f in zip(base, moved, fl):
+            r = np.linalg.norm(m_ - b) / f
+            assert r <= 1.0 + 1e-6
+            worst = max(worst, r)
+    assert worst > 0.05
+
+
+def test_floored_criterion_discounts_only_what_is_below_the_floor():
+    """Exact constant-snap motion (all residuals zero) with every input moved
+    by up to noise of its norm: the derivatives the interpolation then shows
+    are rounding only, the floored criterion sets no bound, while the plain
+    criterion (and the floored one at 1e-4 of the noise) does."""
+    rng = np.random.default_rng(65)
+    noise = 1e-6
+    for _ in range(100):
+        h = 2.0 ** -int(rng.integers(3, 21))
+        a0, j0, s0 = (rng.normal(size=3) for _ in range(3))
+        a1, j1, s1 = a0 + j0 * h + s0 * h * h / 2, j0 + s0 * h, s0.copy()
+        ins = []
+        for q in (a0, j0, s0, a1, j1, s1):
+            dq = rng.normal(size=3)
+            ins.append(q + dq / np.linalg.norm(dq) * 0.9 * noise * np.linalg.norm(q))
+        c, d, e = O.interpolate(h, *ins)
+        a, j, s = ins[3:]
+        assert math.isfinite(O.dt_crit(0.4, a, j, s, c, d, e))
+        assert O.dt_crit_floored(0.4, a, j, s, c, d, e, O.interp_floor(noise, h, *ins)) == math.inf
+        assert math.isfinite(O.dt_crit_floored(0.4, a, j, s, c, d, e,
+                                               O.interp_floor(noise * 1e-4, h, *ins)))
+
+
+def test_block_steps_with_rounding_floors():
+    """The integrator with floors (4e-7, the level set for FP32 pair terms):
+    the run ends with every particle at t_end on steps that are powers of two
+    dividing t, takes no more block steps than without floors, conserves
+    energy as well, and noise = 0 is the criterion as is."""
+    m, x, v = ni.plummer(256, 12)
+    eps = 1e-4
+    E0 = sum(O.energy(m, x, v, eps))
+    plain = O.System(m, x, v, eps)
+    zero = O.System(m, x, v, eps, step_noise=0.0)
+    n_plain, (lt0, _, lh0) = plain.run_until(0.125, log_cap=1 << 16)
+    n_zero, (lt1, _, lh1) = zero.run_until(0.125, log_cap=1 << 16)
+    assert n_zero == n_plain and np.all(lt0 == lt1) and np.all(lh0 == lh1)
+    fl = O.System(m, x, v, eps, step_noise=4e-7)
+    n_fl, _ = fl.run_until(0.125)
+    st = fl.state()
+    assert np.all(st["t"] == 0.125) and np.all(np.mod(st["t"], st["dt"]) == 0.0)
+    k = np.log2(st["dt"])
+    assert np.all(k == np.round(k))
+    assert n_fl <= n_plain
+    E1 = sum(O.energy(m, st["x"], st["v"], eps))
+    assert abs((E1 - E0) / E0) < 1e-9

@@ -152,7 +152,7 @@ void nb_config_default(nb_config *cfg);
  * (eta_s * min(|a|/|j|, sqrt(|a|/|s|)), rounded down to a power of two and
  * clamped to [dt_min, dt_max]; a ratio 0/0, as for a particle under no force,
  * sets no bound, so such a particle starts at dt_max).
- * Errors: NB_EINVAL (n < 1, n > 2^31 - 1, eps <= 0, bad config), NB_ENONFINITE
+ * Errors: NB_EINVAL (n < 1, n > 2^29, eps <= 0, bad config), NB_ENONFINITE
  * (non-finite m, x or v, or m < 0), NB_ENOMEM, NB_ECUDA.  *out is NULL on error. */
 nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
                   const double *v, double eps, const nb_config *cfg);

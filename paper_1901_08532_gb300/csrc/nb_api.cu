@@ -329,8 +329,10 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x, con
         cf = *cfg;
     else
         nb_config_default(&cf);
-    if (n < 1 || n > 0x7fffffffLL) {
-        g_init_err = "n must be in [1, 2^31 - 1]";
+    // 2^29 particles take about 190 GB in any precision; the cap keeps every
+    // per-component index (3 n, and the padded rows) within 32 bits
+    if (n < 1 || n > (int64_t(1) << 29)) {
+        g_init_err = "n must be in [1, 2^29]";
         return NB_EINVAL;
     }
     if (!m || !x || !v) {

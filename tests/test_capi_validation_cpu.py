@@ -58,6 +58,18 @@ def test_invalid_arguments_are_rejected_before_any_cuda_call(kw, msg):
     assert msg in err
 
 
+def test_too_many_particles_are_rejected_before_the_arrays_are_read():
+    """n above 2^29 (about 190 GB of device state) is refused from n alone:
+    the host arrays passed here hold one particle and are never read."""
+    one = np.zeros(3)
+    p = one.ctypes.data_as(C.POINTER(C.c_double))
+    for n in ((1 << 29) + 1, 1 << 31, 1 << 40):
+        ctx = C.c_void_p()
+        st = lib.nb_init(C.byref(ctx), n, p, p, p, 1e-3, C.byref(_cfg()))
+        assert st == nb.NB_EINVAL and not ctx.value
+        assert "n must be" in lib.nb_last_error(None).decode()
+
+
 def test_invalid_tiles_are_rejected():
     cfg_tiles = {"lanes": 3}
     cfg = _cfg()

@@ -26,21 +26,22 @@ def _concat(ms, xs, vs):
     return np.concatenate(ms), np.concatenate(xs), np.concatenate(vs)
 
 
-@pytest.mark.parametrize("prec", [0, 3])
-def test_fp64_and_ex_ensembles_match_oracle_per_system(prec):
+@pytest.mark.parametrize("prec, noise", [(0, 0.0), (3, 0.0), (0, 4e-7)])
+def test_fp64_and_ex_ensembles_match_oracle_per_system(prec, noise):
     """FP64 and EX (double-word) ensembles take the oracle's step decisions
-    system by system and end on its state to 1e-10."""
+    system by system and end on its state to 1e-10; also with the step
+    criterion's rounding floor (FP64, 4e-7 on both sides)."""
     nb = nb_gpu()
     ms, xs, vs = _systems(SIZES)
     eps, t_end = 1e-4, 0.125
-    ens = nb.Ensemble(SIZES, *_concat(ms, xs, vs), eps, precision=prec)
+    ens = nb.Ensemble(SIZES, *_concat(ms, xs, vs), eps, precision=prec, step_noise=noise)
     ens.run(t_end)
     st = ens.state()
     steps, inter, _ = ens.stats()
     ens.close()
     o = 0
     for k, n in enumerate(SIZES):
-        ref = O.System(ms[k], xs[k], vs[k], eps)
+        ref = O.System(ms[k], xs[k], vs[k], eps, step_noise=noise)
         nsteps, _ = ref.run_until(t_end)
         sr = ref.state()
         assert steps[k] == nsteps, (k, steps[k], nsteps)

@@ -615,10 +615,10 @@ nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req, int6
     nb_tiles t = req;
     const bool ex = c->cfg.precision == NB_EX;
     const bool mixed = nb_fp32_eval(c->cfg.precision);
-    // defaults from the launch-shape sweep on GB300 (autotune.py): mixed
-    // KI = 2 with four j per iteration; larger blocks and tiles once the
-    // active set fills the grid without splitting
-    const bool big = n_act >= 16384;
+    // defaults from the launch-shape sweeps on GB300 (autotune.py): mixed
+    // KI = 2 with four j per iteration for small active sets, three
+    // i-particles per thread and 512-j tiles from 8192 active on
+    const bool big = n_act >= 8192;
     if (t.ki <= 0)
         t.ki = mixed ? (big ? 3 : 2) : 1;
     if (t.threads <= 0)
@@ -632,7 +632,7 @@ nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req, int6
         t.lanes = l;
     }
     if (t.jtile <= 0)
-        t.jtile = mixed ? (big ? 512 : 256) : (ex ? 512 : 256);
+        t.jtile = mixed ? (n_act >= 4096 ? 512 : 256) : (ex ? 512 : 256);
     if ((mixed || ex) && t.jtile % 4)
         t.jtile = (t.jtile / 4 + 1) * 4;   // whole 16-byte rows per bulk copy
     if (t.split <= 0) {

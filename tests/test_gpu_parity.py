@@ -351,3 +351,36 @@ def test_bench_headline_launch_sampled_parity():
     kap = O.evaluate_kappa(m, x, v, a, eps, pick)
     for gq, rq, kq in zip(got, ref, kap):
         assert check_parity(1, gq[pick], rq, kq) <= 1.0
+
+
+@pytest.fixture(scope="module")
+def large_system():
+    n, eps = 1 << 24, 1e-4
+    m, x, v = ni.plummer(n, 17, imf="salpeter")
+    a = ni.random_state(n, 18, scale=2.0)
+    act = ni.active_subset(n, 1024, 19)
+    pick = np.array([0, 341, 682, 1023])
+    ref = O.evaluate(m, x, v, a, eps, act[pick])
+    kap = O.evaluate_kappa(m, x, v, a, eps, act[pick])
+    return m, x, v, a, eps, act, pick, ref, kap
+
+
+@pytest.mark.parametrize("prec", [0, 1, 3])
+def test_large_system_sampled_parity(prec, large_system):
+    """N = 2^24, sixteen times the benchmark's N (about 6 GB of device
+    state), Plummer with Salpeter masses, eps = 1e-4, a seeded acceleration
+    field, 1024 active particles in the automatic launch shape: 4 sampled
+    particles against the oracle (FP64 1e-12 per component of |ref|; mixed
+    1e-6 and EX 1e-12 of sum_j |T_ij|)."""
+    nb = nb_gpu()
+    m, x, v, a, eps, act, pick, ref, kap = large_system
+    g = nb.NBody(m, x, v, eps, precision=prec, start_forces=False)
+    g.set_state({"a": a})
+    g.predict(0.0)
+    got = g.evaluate(act)
+    g.close()
+    for gq, rq, kq in zip(got, ref, kap):
+        if prec == 0:
+            assert check_parity(0, gq[pick], rq) <= 1.0
+        else:
+            assert check_parity(1, gq[pick], rq, kq, tol_mixed=1e-6 if prec == 1 else 1e-12) <= 1.0

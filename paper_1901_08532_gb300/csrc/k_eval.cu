@@ -626,13 +626,16 @@ nb_tiles nb_auto_tiles(const nb_ctx *c, int64_t n_act, const nb_tiles &req, int6
     if (t.junroll <= 0)
         t.junroll = ex ? 2 : 4;
     if (t.lanes <= 0) {
-        int l = 1;
+        // two lanes per i-particle below 4096 active in the mixed kernel
+        // (fewer, deeper j-chunks to fold); more while the block would hold
+        // more i-slots than there are active particles
+        int l = mixed && t.ki == 2 && n_act < 4096 ? 2 : 1;
         while (l < 32 && static_cast<int64_t>(t.threads / (2 * l)) * t.ki >= n_act)
             l *= 2;
         t.lanes = l;
     }
     if (t.jtile <= 0)
-        t.jtile = mixed ? (n_act >= 4096 ? 512 : 256) : (ex ? 512 : 256);
+        t.jtile = mixed ? (n_act >= 512 ? 512 : 256) : (ex ? 512 : 256);
     if ((mixed || ex) && t.jtile % 4)
         t.jtile = (t.jtile / 4 + 1) * 4;   // whole 16-byte rows per bulk copy
     if (t.split <= 0) {

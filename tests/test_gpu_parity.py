@@ -28,6 +28,7 @@ SHAPES = [
     {"ki": 2, "threads": 128, "jtile": 60, "lanes": 1, "split": 5, "junroll": 4},
     {"ki": 3, "threads": 128, "jtile": 512, "lanes": 1, "split": 2, "junroll": 4},
     {"ki": 3, "threads": 64, "jtile": 256, "lanes": 2, "split": 1, "junroll": 4},
+    {"ki": 2, "threads": 128, "jtile": 512, "lanes": 2, "split": 3, "junroll": 4},
 ]
 
 

@@ -421,7 +421,9 @@ def run_ours(args):
     value = interactions / elapsed
     eval_s = sum(eval_ms) / len(eval_ms) / 1e3
     achieved = FLOPS_PER_INTERACTION * float(n) * (hi - lo) / eval_s / 1e12
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernel_sha"] == _kernel_sha() else None
+    # the DRAM figure is of the whole-range launch; a rank's j-range launch is another workload
+    traffic = (TRAFFIC["bytes_per_launch"] if TRAFFIC["kernel_sha"] == _kernel_sha() and not split
+               else None)
     clocks = clk.summary()
     peaks = measure_peaks(nb, torch)
     peak_meas = peaks["fp32_tflops_at_max_clock"]

@@ -581,9 +581,10 @@ def secondary(nb, np, torch, m, x, v, st, stream, n):
 def error_vs_oracle(nb, np, torch, m, x, v, stream, act, sums, kap):
     """Both GPU precisions on the oracle's sample (same inputs: the start
     positions and velocities, the seeded acceleration field of
-    oracle_accel, t = 0): per particle |d|_inf / |ref|_2 (max and the
-    fraction above 1e-6), and |d|_inf / sum_j |T_ij| (the error relative to
-    the sum's condition number)."""
+    oracle_accel, t = 0; the mixed path in the headline's all-active launch,
+    the FP64 path on the sample alone): per particle |d|_inf / |ref|_2 (max
+    and the fraction above 1e-6), and |d|_inf / sum_j |T_ij| (the error
+    relative to the sum's condition number)."""
     import nb_inputs as ni
     out = {"sample": int(len(act)),
            "inputs": "start positions and velocities, seeded acceleration field (uniform [-2, 2])"}
@@ -592,7 +593,11 @@ def error_vs_oracle(nb, np, torch, m, x, v, stream, act, sums, kap):
         ctx = nb.NBody(m, x, v, EPS, precision=prec, stream=stream, start_forces=False)
         ctx.set_state({"a": a})
         ctx.predict(0.0)
-        got = ctx.evaluate(act)
+        if prec == nb.NB_MIXED:
+            # the headline's own launch (every particle active), read at the sample
+            got = [q[act] for q in ctx.evaluate(None)]
+        else:
+            got = ctx.evaluate(act)
         ctx.close()
         rec = {}
         for q, g, r, k in zip(("acc", "jerk", "snap"), got, sums, kap):

@@ -415,24 +415,28 @@ __device__ bool eval_share(const EnsArgs &a, int off, int j0, int j1, int s0, in
                               (static_cast<double>(part[q].h.y) + static_cast<double>(part[q].l.y));
             } else if (MIXED) {
                 const float *s = reinterpret_cast<const float *>(smem) + static_cast<size_t>(stg) * NCF * jt;
-                float2 part[9];
+                // FP32 running sums over at most kMixedFoldJ j per lane
+                for (int f0 = 0; f0 < len; f0 += kMixedFoldJ * lanes) {
+                    const int f1 = min(len, f0 + kMixedFoldJ * lanes);
+                    float2 part[9];
 #pragma unroll
-                for (int q = 0; q < 9; ++q)
-                    part[q] = f2(0.0f);
-                for (int jj = 4 * lj; jj < len; jj += 4 * lanes) {
-                    float2 c0[NCF], c1[NCF];
+                    for (int q = 0; q < 9; ++q)
+                        part[q] = f2(0.0f);
+                    for (int jj = f0 + 4 * lj; jj < f1; jj += 4 * lanes) {
+                        float2 c0[NCF], c1[NCF];
 #pragma unroll
-                    for (int r = 0; r < NCF; ++r) {
-                        const float4 w = *reinterpret_cast<const float4 *>(s + r * jt + jj);
-                        c0[r] = make_float2(w.x, w.y);
-                        c1[r] = make_float2(w.z, w.w);
+                        for (int r = 0; r < NCF; ++r) {
+                            const float4 w = *reinterpret_cast<const float4 *>(s + r * jt + jj);
+                            c0[r] = make_float2(w.x, w.y);
+                            c1[r] = make_float2(w.z, w.w);
+                        }
+                        pair_mixed2(c0, ni, f2(static_cast<float>(a.eps2)), part);
+                        pair_mixed2(c1, ni, f2(static_cast<float>(a.eps2)), part);
                     }
-                    pair_mixed2(c0, ni, f2(static_cast<float>(a.eps2)), part);
-                    pair_mixed2(c1, ni, f2(static_cast<float>(a.eps2)), part);
-                }
 #pragma unroll
-                for (int q = 0; q < 9; ++q)
-                    two_sum_acc(hi[q], lo[q], __fadd_rn(part[q].x, part[q].y));
+                    for (int q = 0; q < 9; ++q)
+                        two_sum_acc(hi[q], lo[q], __fadd_rn(part[q].x, part[q].y));
+                }
             } else {
                 const double2 *s = reinterpret_cast<const double2 *>(smem) + static_cast<size_t>(stg) * 5 * jt;
                 double part[9];

@@ -346,61 +346,66 @@ __global__ void __launch_bounds__(mixed_max_threads(KI), mixed_min_blocks(KI))
         }
         const int len = min(jt, jend - (jbeg + tl * jt));
         const float *s = reinterpret_cast<const float *>(smem) + static_cast<size_t>(st) * NCF * jt;
+        // FP32 running sums over at most kMixedFoldJ j per lane, then folded
+        // into the compensated sums
+        for (int f0 = 0; f0 < len; f0 += nbk::kMixedFoldJ * lanes) {
+            const int f1 = min(len, f0 + nbk::kMixedFoldJ * lanes);
 #pragma unroll
-        for (int k = 0; k < KI; ++k)
+            for (int k = 0; k < KI; ++k)
 #pragma unroll
-            for (int q = 0; q < 9; ++q)
-                part[q][k] = f2(0.0f);
-        for (int jj = JU * lj; jj < len; jj += JU * lanes) {
-            if (JU == 4) {
-                float2 c0[NCF], c1[NCF];
+                for (int q = 0; q < 9; ++q)
+                    part[q][k] = f2(0.0f);
+            for (int jj = f0 + JU * lj; jj < f1; jj += JU * lanes) {
+                if (JU == 4) {
+                    float2 c0[NCF], c1[NCF];
 #pragma unroll
-                for (int r = 0; r < NCF; ++r) {
-                    const float4 w = *reinterpret_cast<const float4 *>(s + r * jt + jj);
-                    c0[r] = make_float2(w.x, w.y);
-                    c1[r] = make_float2(w.z, w.w);
-                }
+                    for (int r = 0; r < NCF; ++r) {
+                        const float4 w = *reinterpret_cast<const float4 *>(s + r * jt + jj);
+                        c0[r] = make_float2(w.x, w.y);
+                        c1[r] = make_float2(w.z, w.w);
+                    }
 #pragma unroll
-                for (int k = 0; k < KI; ++k) {
-                    float2 pk[9];
+                    for (int k = 0; k < KI; ++k) {
+                        float2 pk[9];
 #pragma unroll
-                    for (int q = 0; q < 9; ++q)
-                        pk[q] = part[q][k];
-                    pair_mixed2(c0, ni[k], eps2, pk);
-                    pair_mixed2(c1, ni[k], eps2, pk);
+                        for (int q = 0; q < 9; ++q)
+                            pk[q] = part[q][k];
+                        pair_mixed2(c0, ni[k], eps2, pk);
+                        pair_mixed2(c1, ni[k], eps2, pk);
 #pragma unroll
-                    for (int q = 0; q < 9; ++q)
-                        part[q][k] = pk[q];
-                }
-            } else {
-                float2 c0[NCF];
+                        for (int q = 0; q < 9; ++q)
+                            part[q][k] = pk[q];
+                    }
+                } else {
+                    float2 c0[NCF];
 #pragma unroll
-                for (int r = 0; r < NCF; ++r)
-                    c0[r] = *reinterpret_cast<const float2 *>(s + r * jt + jj);
+                    for (int r = 0; r < NCF; ++r)
+                        c0[r] = *reinterpret_cast<const float2 *>(s + r * jt + jj);
 #pragma unroll
-                for (int k = 0; k < KI; ++k) {
-                    float2 pk[9];
+                    for (int k = 0; k < KI; ++k) {
+                        float2 pk[9];
 #pragma unroll
-                    for (int q = 0; q < 9; ++q)
-                        pk[q] = part[q][k];
-                    pair_mixed2(c0, ni[k], eps2, pk);
+                        for (int q = 0; q < 9; ++q)
+                            pk[q] = part[q][k];
+                        pair_mixed2(c0, ni[k], eps2, pk);
 #pragma unroll
-                    for (int q = 0; q < 9; ++q)
-                        part[q][k] = pk[q];
+                        for (int q = 0; q < 9; ++q)
+                            part[q][k] = pk[q];
+                    }
                 }
             }
+            // fold the FP32 sums (both halves) into the compensated accumulators
+#pragma unroll
+            for (int k = 0; k < KI; ++k)
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    float h = acc_s[(q * KI + k) * nthr + tid];
+                    float l = acc_s[((9 + q) * KI + k) * nthr + tid];
+                    nbk::two_sum_acc(h, l, __fadd_rn(part[q][k].x, part[q][k].y));
+                    acc_s[(q * KI + k) * nthr + tid] = h;
+                    acc_s[((9 + q) * KI + k) * nthr + tid] = l;
+                }
         }
-        // fold the FP32 tile sums (both halves) into the compensated accumulators
-#pragma unroll
-        for (int k = 0; k < KI; ++k)
-#pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                float h = acc_s[(q * KI + k) * nthr + tid];
-                float l = acc_s[((9 + q) * KI + k) * nthr + tid];
-                nbk::two_sum_acc(h, l, __fadd_rn(part[q][k].x, part[q][k].y));
-                acc_s[(q * KI + k) * nthr + tid] = h;
-                acc_s[((9 + q) * KI + k) * nthr + tid] = l;
-            }
         __syncthreads();
         if (tid == 0 && tl + 2 < ntiles) {
             issue_tile_rows(smem, bar, a, st, jbeg + (tl + 2) * jt, min(jt, jend - (jbeg + (tl + 2) * jt)));

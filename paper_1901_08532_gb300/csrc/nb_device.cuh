@@ -82,6 +82,15 @@ __device__ __forceinline__ float rcp_est(float x)
     return y;
 }
 
+// j per lane summed in FP32 (kMixedFoldJ / 2 terms in each half of a packed
+// pair) before each fold into the compensated sums.  The FP32 rounding of a
+// running sum grows with its length: over all 2^20 particles of the
+// Plummer/Salpeter model, 256 j per fold left 32 snaps above 1e-6 of their
+// condition number sum_j |S_ij| and whole 512-j tiles 369; 128 j leaves 9
+// (at most 1.11e-6, the rest of that error being the pair terms' own FP32
+// rounding), for 1.4 % more time than 256.
+constexpr int kMixedFoldJ = 128;
+
 // Two pair terms (j, j+1) for one i.  c[] are the 13 j-rows (as pairs), ni[]
 // the negated i-values (-xh,-yh,-zh,-xl,-yl,-zl,-vx,-vy,-vz,-ax,-ay,-az).
 // With r, v, a = j - i, R = r.r + eps^2, q = R^(-1/2), mu = m_j q^3,

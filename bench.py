@@ -137,6 +137,9 @@ def parse():
     p.add_argument("--step-noise", type=float, default=0.0,
                    help="nb_config.step_noise for --integrate and --ensemble (the rounding floor the "
                         "step criterion discounts; 0: the criterion as is)")
+    p.add_argument("--census", action="store_true",
+                   help="mixed error over every particle of the default model (--n) in units of the "
+                        "sums' condition numbers, against the FP64 GPU path (about two minutes at 2^20)")
     p.add_argument("--peaks", action="store_true",
                    help="throughput probes of the CUDA-core pipes (FP32 FMA scalar and f32x2, FP64 "
                         "FMA, special-function estimates, and packed FMAs mixed with estimates)")
@@ -1060,10 +1063,55 @@ def peaks_bench(args):
     return 0
 
 
+def census_bench(args):
+    """The mixed path's error over every particle of the headline model
+    (Plummer with Salpeter masses, eps 1e-4, seed 3, the seeded acceleration
+    field of the oracle comparison, t = 0, every particle active, the
+    headline launch): |d|_inf against the FP64 GPU path (whose own error is
+    about 1e-15) in units of each sum's condition number sum_j |T_ij|
+    (nb_evaluate_kappa), and in the plain reading |d|_inf / |ref|_2."""
+    import numpy as np
+    import torch
+
+    import nb_inputs as ni
+    import paper_1901_08532_gb300 as nb
+    n = args.n
+    torch.cuda.set_device(0)
+    m, x, v = ni.plummer(n, SEED, imf="salpeter")
+    a = oracle_accel(ni, n)
+    res = {}
+    for name, prec in (("fp64", nb.NB_FP64), ("mixed", nb.NB_MIXED)):
+        ctx = nb.NBody(m, x, v, EPS, precision=prec, start_forces=False)
+        ctx.set_state({"a": a})
+        ctx.predict(0.0)
+        t0 = time.perf_counter()
+        res[name] = ctx.evaluate(None)
+        res[name + "_s"] = time.perf_counter() - t0
+        if prec == nb.NB_MIXED:
+            res["kappa"] = ctx.evaluate_kappa(None)
+            res["tiles"] = ctx.resolve_tiles(n)
+        ctx.close()
+    out = {"census": f"plummer_salpeter_N{n}_eps1e-4_all_active", "particles": n,
+           "reference": "FP64 GPU path", "mixed_tiles": res["tiles"],
+           "seconds": {"fp64": res["fp64_s"], "mixed": res["mixed_s"]}}
+    for q, name in enumerate(("acc", "jerk", "snap")):
+        d = np.abs(res["mixed"][q] - res["fp64"][q]).max(axis=1)
+        r = d / res["kappa"][q]
+        plain = d / np.linalg.norm(res["fp64"][q], axis=1)
+        out[name] = {"kappa_norm_max": float(r.max()),
+                     "above": {f"{t:g}": int((r > t).sum()) for t in (5e-7, 8e-7, 1e-6)},
+                     "p999": float(np.quantile(r, 0.999)),
+                     "plain_above_1e-6": float((plain > 1e-6).mean())}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.peaks:
         return peaks_bench(args)
+    if args.census:
+        return census_bench(args)
     if args.precision_study:
         return precision_study(args)
     if args.integrate:

@@ -219,6 +219,22 @@ nb_status nb_evaluate_partial(nb_ctx *ctx, const int32_t *active, int64_t n_act,
 nb_status nb_set_forces(nb_ctx *ctx, const int32_t *active, int64_t n_act, int active_on_device,
                         const double *f, int f_on_device);
 
+/* Condition numbers of the evaluation's sums (section 3 item 4: a, jerk and
+ * snap are sums over j of pair terms A_ij, J_ij, S_ij) for the n_act
+ * particles listed in active[] (as in nb_evaluate; NULL means all n):
+ * kappa[q * n_act + k] = sum_j |T_ij| for T = A, J, S (q = 0, 1, 2; vector
+ * norms) against the predicted j-particles of the last nb_predict.  They
+ * scale the error bound of each sum (the mixed path's bound is 1e-6 kappa).
+ * A diagnostic: one thread per listed particle, FP32 pair terms with
+ * two-part position differences, relative accuracy about 1e-6; any
+ * precision.  kappa is a host pointer (the call then synchronises) or a
+ * device pointer when out_on_device != 0.  Does not touch the context's
+ * evaluation results or active set.
+ * Errors: NB_EINVAL (n_act < 0 or > n, bad index, NULL kappa), NB_ESTATE
+ * (no prediction yet), NB_ECUDA. */
+nb_status nb_evaluate_kappa(nb_ctx *ctx, const int32_t *active, int64_t n_act, int active_on_device,
+                            double *kappa, int out_on_device);
+
 /* Corrector (section 3) for the particles of the last nb_evaluate (or
  * nb_set_forces), whose prediction time must equal t: corrected x and v, the
  * new a/jerk/snap,

@@ -70,6 +70,7 @@ _lib.nb_correct.argtypes = [_vp, C.c_double]
 _lib.nb_schedule.argtypes = [_vp, _d, _i64]
 _lib.nb_evaluate_partial.argtypes = [_vp, _vp, C.c_int64, C.c_int, C.c_int64, C.c_int64, _vp, C.c_int]
 _lib.nb_set_forces.argtypes = [_vp, _vp, C.c_int64, C.c_int, _vp, C.c_int]
+_lib.nb_evaluate_kappa.argtypes = [_vp, _vp, C.c_int64, C.c_int, _vp, C.c_int]
 _lib.nb_step.argtypes = [_vp, _d, _i64]
 _lib.nb_run_until.argtypes = [_vp, C.c_double, _i64, C.c_int64, _d, _i64]
 _lib.nb_run_diag.argtypes = [_vp, C.c_double, C.c_double, C.c_int64, _d, _i64, _i64]
@@ -122,14 +123,14 @@ _lib.nb_last_error.restype = C.c_char_p
 _lib.nb_free.argtypes = [_vp]
 _lib.nb_free.restype = None
 for _f in ("nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_correct", "nb_step", "nb_run_until",
-           "nb_schedule", "nb_evaluate_partial", "nb_set_forces",
+           "nb_schedule", "nb_evaluate_partial", "nb_set_forces", "nb_evaluate_kappa",
            "nb_run_diag",
            "nb_energy", "nb_angmom", "nb_get_state", "nb_set_state", "nb_get_active",
            "nb_set_tiles", "nb_resolve_tiles", "nb_counters"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("nb_config_default", "nb_init", "nb_predict", "nb_get_predicted", "nb_evaluate", "nb_correct", "nb_step",
-            "nb_schedule", "nb_evaluate_partial", "nb_set_forces",
+            "nb_schedule", "nb_evaluate_partial", "nb_set_forces", "nb_evaluate_kappa",
             "nb_run_until", "nb_run_diag", "nb_energy", "nb_angmom", "nb_get_state", "nb_set_state",
             "nb_get_active", "nb_set_tiles", "nb_resolve_tiles", "nb_counters", "nb_inject_fault",
             "nb_evaluate_fp64_static", "nb_last_error", "nb_free", "nb_ensemble_init",
@@ -329,6 +330,15 @@ class NBody:
             f = np.ascontiguousarray(f, dtype=np.float64)
             fptr, fdev = f.ctypes.data, 0
         self._check(_lib.nb_set_forces(self._ctx, aptr, n_act, on_dev, fptr, fdev))
+
+    def evaluate_kappa(self, active=None):
+        """Condition numbers (sum_j |A_ij|, sum_j |J_ij|, sum_j |S_ij|) of the
+        active particles' sums at the last prediction, three numpy arrays
+        [n_act] (nb_evaluate_kappa)."""
+        aptr, n_act, on_dev, keep = self._active_arg(active, self.n)
+        out = np.zeros((3, max(1, n_act)))
+        self._check(_lib.nb_evaluate_kappa(self._ctx, aptr, n_act, on_dev, out.ctypes.data, 0))
+        return tuple(out[q, :n_act].copy() for q in range(3))
 
     # --- integration --------------------------------------------------------
     def step(self):

@@ -659,6 +659,53 @@ nb_status nb_set_forces(nb_ctx *c, const int32_t *active, int64_t n_act, int act
     return NB_OK;
 }
 
+nb_status nb_evaluate_kappa(nb_ctx *c, const int32_t *active, int64_t n_act, int active_on_device,
+                            double *kappa, int out_on_device)
+{
+    CHECK_CTX(c);
+    if (!c->have_pred)
+        return fail(c, NB_ESTATE, "nb_evaluate_kappa needs a prediction (nb_predict) first");
+    if (n_act < 0 || n_act > c->n)
+        return fail(c, NB_EINVAL, "n_act must be in [0, n]");
+    if (!active && n_act != c->n)
+        return fail(c, NB_EINVAL, "active == NULL requires n_act == n");
+    if (!kappa && n_act > 0)
+        return fail(c, NB_EINVAL, "kappa must not be NULL");
+    if (active && !active_on_device)
+        for (int64_t k = 0; k < n_act; ++k)
+            if (active[k] < 0 || active[k] >= c->n)
+                return fail(c, NB_EINVAL, "active index out of range");
+    if (n_act == 0)
+        return NB_OK;
+    // stream-ordered scratch for a host (or implied) active list and for
+    // results bound for the host; the context's own buffers stay untouched
+    const bool own_act = !(active && active_on_device);
+    const size_t act_bytes = own_act ? (static_cast<size_t>(n_act) * sizeof(int32_t) + 15) / 16 * 16 : 0;
+    const size_t out_bytes = out_on_device ? 0 : static_cast<size_t>(3 * n_act) * sizeof(double);
+    void *tmp = nullptr;
+    if (act_bytes + out_bytes > 0)
+        CU(c, cudaMallocAsync(&tmp, act_bytes + out_bytes, c->stream));
+    const int32_t *act_d = active;
+    if (own_act) {
+        int32_t *a = static_cast<int32_t *>(tmp);
+        if (active)
+            CU(c, cudaMemcpyAsync(a, active, static_cast<size_t>(n_act) * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, c->stream));
+        else
+            CU(c, nb_launch_iota(c, static_cast<int>(c->n), a));
+        act_d = a;
+    }
+    double *out_d = out_on_device ? kappa : reinterpret_cast<double *>(static_cast<char *>(tmp) + act_bytes);
+    CU(c, nb_launch_kappa(c, act_d, static_cast<int>(n_act), out_d));
+    if (!out_on_device)
+        CU(c, cudaMemcpyAsync(kappa, out_d, out_bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (tmp)
+        CU(c, cudaFreeAsync(tmp, c->stream));
+    if (!out_on_device)
+        CU(c, cudaStreamSynchronize(c->stream));
+    return NB_OK;
+}
+
 nb_status nb_correct(nb_ctx *c, double t)
 {
     CHECK_CTX(c);

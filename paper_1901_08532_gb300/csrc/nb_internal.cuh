@@ -240,3 +240,6 @@ cudaError_t nb_run_stepper(nb_ctx *c, double t_end, int64_t log_cap, int64_t log
 // k_energy.cu
 cudaError_t nb_launch_energy(nb_ctx *c, double *ek_pe_dev);
 cudaError_t nb_launch_angmom(nb_ctx *c, double *l4_dev);
+// k_kappa.cu: condition numbers sum_j |A_ij|, |J_ij|, |S_ij| of the listed
+// particles against the predicted j-buffer, out_dev [3][n_act].
+cudaError_t nb_launch_kappa(nb_ctx *c, const int32_t *act_dev, int n_act, double *out_dev);

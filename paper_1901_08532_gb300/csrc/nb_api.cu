@@ -682,12 +682,21 @@ nb_status nb_evaluate_kappa(nb_ctx *c, const int32_t *active, int64_t n_act, int
     const bool own_act = !(active && active_on_device);
     const size_t act_bytes = own_act ? (static_cast<size_t>(n_act) * sizeof(int32_t) + 15) / 16 * 16 : 0;
     const size_t out_bytes = out_on_device ? 0 : static_cast<size_t>(3 * n_act) * sizeof(double);
-    void *tmp = nullptr;
+    struct Scratch {  // released on every return path, in stream order
+        void *p = nullptr;
+        cudaStream_t s = nullptr;
+        ~Scratch()
+        {
+            if (p)
+                cudaFreeAsync(p, s);
+        }
+    } tmp;
+    tmp.s = c->stream;
     if (act_bytes + out_bytes > 0)
-        CU(c, cudaMallocAsync(&tmp, act_bytes + out_bytes, c->stream));
+        CU(c, cudaMallocAsync(&tmp.p, act_bytes + out_bytes, c->stream));
     const int32_t *act_d = active;
     if (own_act) {
-        int32_t *a = static_cast<int32_t *>(tmp);
+        int32_t *a = static_cast<int32_t *>(tmp.p);
         if (active)
             CU(c, cudaMemcpyAsync(a, active, static_cast<size_t>(n_act) * sizeof(int32_t),
                                   cudaMemcpyHostToDevice, c->stream));
@@ -695,14 +704,12 @@ nb_status nb_evaluate_kappa(nb_ctx *c, const int32_t *active, int64_t n_act, int
             CU(c, nb_launch_iota(c, static_cast<int>(c->n), a));
         act_d = a;
     }
-    double *out_d = out_on_device ? kappa : reinterpret_cast<double *>(static_cast<char *>(tmp) + act_bytes);
+    double *out_d = out_on_device ? kappa : reinterpret_cast<double *>(static_cast<char *>(tmp.p) + act_bytes);
     CU(c, nb_launch_kappa(c, act_d, static_cast<int>(n_act), out_d));
-    if (!out_on_device)
+    if (!out_on_device) {
         CU(c, cudaMemcpyAsync(kappa, out_d, out_bytes, cudaMemcpyDeviceToHost, c->stream));
-    if (tmp)
-        CU(c, cudaFreeAsync(tmp, c->stream));
-    if (!out_on_device)
         CU(c, cudaStreamSynchronize(c->stream));
+    }
     return NB_OK;
 }
 

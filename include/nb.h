@@ -228,8 +228,9 @@ nb_status nb_set_forces(nb_ctx *ctx, const int32_t *active, int64_t n_act, int a
  * A diagnostic: one thread per listed particle, FP32 pair terms with
  * two-part position differences, relative accuracy about 1e-6; any
  * precision.  kappa is a host pointer (the call then synchronises) or a
- * device pointer when out_on_device != 0.  Does not touch the context's
- * evaluation results or active set.
+ * device pointer when out_on_device != 0.  Indices are checked on the host
+ * when active is a host pointer; device lists are trusted.  Does not touch
+ * the context's evaluation results or active set.
  * Errors: NB_EINVAL (n_act < 0 or > n, bad index, NULL kappa), NB_ESTATE
  * (no prediction yet), NB_ECUDA. */
 nb_status nb_evaluate_kappa(nb_ctx *ctx, const int32_t *active, int64_t n_act, int active_on_device,

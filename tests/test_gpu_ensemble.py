@@ -256,3 +256,42 @@ def test_full_size_ensemble_sampled_systems_match_oracle():
         np.testing.assert_array_equal(st["dt"][sl], sr["dt"])
         for f in ("x", "v"):
             assert rel_err(st[f][sl], sr[f]).max() < 1e-10, (k, f, rel_err(st[f][sl], sr[f]).max())
+
+
+def test_full_size_mixed_ensemble_with_rounding_floor():
+    """The 256-system ensemble at full size in the mixed form (FP32 pair
+    terms, FP64 prediction and correction) with the step criterion's
+    rounding floor at 4e-7, the bench's configuration, to t = 1/4: the
+    sampled systems (the three smallest, those nearest 1000 and 2000
+    particles) end at t = 1/4 on power-of-two steps that divide it, take no
+    more block steps than the oracle's own FP64 run of the same system, and
+    conserve energy (the oracle's energy of the final state) to within ten
+    times that FP64 run's error plus 2e-9 (measured: 1.3e-9 to 9.6e-9
+    against 1.3e-10 to 5.7e-9 for FP64)."""
+    nb = nb_gpu()
+    eps, t_end = 1e-4, 0.25
+    sizes = ni.ensemble_sizes(256, 4)
+    parts = [ni.plummer(int(k), 1000 + q) for q, k in enumerate(sizes)]
+    ens = nb.Ensemble(sizes, *[np.concatenate([p[f] for p in parts]) for f in range(3)], eps,
+                      precision=nb.NB_MIXED, step_noise=4e-7)
+    ens.run(t_end)
+    st = ens.state()
+    steps, _, _ = ens.stats()
+    ens.close()
+    order = np.argsort(sizes)
+    pick = [int(order[0]), int(order[1]), int(order[2]), int(np.argmin(np.abs(sizes - 1000))),
+            int(np.argmin(np.abs(sizes - 2000)))]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    for k in pick:
+        sl = slice(int(offs[k]), int(offs[k + 1]))
+        m, x, v = parts[k]
+        assert np.all(st["t"][sl] == t_end)
+        assert np.all(np.fmod(st["t"][sl], st["dt"][sl]) == 0.0)
+        ref = O.System(m, x, v, eps)
+        nsteps, _ = ref.run_until(t_end)
+        sr = ref.state()
+        E0 = sum(O.energy(m, x, v, eps))
+        de_ref = abs((sum(O.energy(m, sr["x"], sr["v"], eps)) - E0) / E0)
+        de = abs((sum(O.energy(m, st["x"][sl], st["v"][sl], eps)) - E0) / E0)
+        assert steps[k] <= nsteps, (k, steps[k], nsteps)
+        assert de <= 10 * de_ref + 2e-9, (k, de, de_ref)

@@ -29,7 +29,11 @@ def test_partial_sums_over_tiled_ranges_match_oracle(prec):
     total = np.zeros((9, act.size))
     for r in range(3):
         lo, hi = shard_bounds(n, 3, r, align)
+        _, before = g.counters()
         part = g.evaluate_partial(act, lo, hi, out="host" if r == 1 else "device")
+        _, after = g.counters()
+        # a rank's share counts its own interactions (the bench sums them over the ranks)
+        assert after - before == act.size * (hi - lo)
         total += part if r == 1 else part.cpu().numpy()
     empty = g.evaluate_partial(act, 8, 8, out="host")      # an empty range adds nothing
     assert not empty.any()

@@ -1064,12 +1064,13 @@ def peaks_bench(args):
 
 
 def census_bench(args):
-    """The mixed path's error over every particle of the headline model
-    (Plummer with Salpeter masses, eps 1e-4, seed 3, the seeded acceleration
-    field of the oracle comparison, t = 0, every particle active, the
-    headline launch): |d|_inf against the FP64 GPU path (whose own error is
-    about 1e-15) in units of each sum's condition number sum_j |T_ij|
-    (nb_evaluate_kappa), and in the plain reading |d|_inf / |ref|_2."""
+    """The mixed and EX paths' errors over every particle of the headline
+    model (Plummer with Salpeter masses, eps 1e-4, seed 3, the seeded
+    acceleration field of the oracle comparison, t = 0, every particle
+    active, the mixed path in the headline launch): |d|_inf against the FP64
+    GPU path (whose own error is about 1e-15) in units of each sum's
+    condition number sum_j |T_ij| (nb_evaluate_kappa), and in the plain
+    reading |d|_inf / |ref|_2; counts against 1e-6 (mixed) and 1e-12 (EX)."""
     import numpy as np
     import torch
 
@@ -1080,7 +1081,7 @@ def census_bench(args):
     m, x, v = ni.plummer(n, SEED, imf="salpeter")
     a = oracle_accel(ni, n)
     res = {}
-    for name, prec in (("fp64", nb.NB_FP64), ("mixed", nb.NB_MIXED)):
+    for name, prec in (("fp64", nb.NB_FP64), ("mixed", nb.NB_MIXED), ("ex", nb.NB_EX)):
         ctx = nb.NBody(m, x, v, EPS, precision=prec, start_forces=False)
         ctx.set_state({"a": a})
         ctx.predict(0.0)
@@ -1091,17 +1092,33 @@ def census_bench(args):
             res["kappa"] = ctx.evaluate_kappa(None)
             res["tiles"] = ctx.resolve_tiles(n)
         ctx.close()
+    # the FP64 path once more on the inputs rounded to double words (hi + lo
+    # FP32, as the EX buffer holds them): what separates EX's arithmetic from
+    # its 48-bit representation of the inputs
+    def dw(q):
+        h = q.astype(np.float32).astype(np.float64)
+        return h + (q - h).astype(np.float32).astype(np.float64)
+    ctx = nb.NBody(dw(m), dw(x), dw(v), EPS, precision=nb.NB_FP64, start_forces=False)
+    ctx.set_state({"a": dw(a)})
+    ctx.predict(0.0)
+    res["fp64_dw"] = ctx.evaluate(None)
+    ctx.close()
     out = {"census": f"plummer_salpeter_N{n}_eps1e-4_all_active", "particles": n,
-           "reference": "FP64 GPU path", "mixed_tiles": res["tiles"],
-           "seconds": {"fp64": res["fp64_s"], "mixed": res["mixed_s"]}}
-    for q, name in enumerate(("acc", "jerk", "snap")):
-        d = np.abs(res["mixed"][q] - res["fp64"][q]).max(axis=1)
-        r = d / res["kappa"][q]
-        plain = d / np.linalg.norm(res["fp64"][q], axis=1)
-        out[name] = {"kappa_norm_max": float(r.max()),
-                     "above": {f"{t:g}": int((r > t).sum()) for t in (5e-7, 8e-7, 1e-6)},
-                     "p999": float(np.quantile(r, 0.999)),
-                     "plain_above_1e-6": float((plain > 1e-6).mean())}
+           "reference": "FP64 GPU path (ex_arith: on the double-word-rounded inputs)",
+           "mixed_tiles": res["tiles"],
+           "seconds": {k: res[k + "_s"] for k in ("fp64", "mixed", "ex")}}
+    for path, ref, bound in (("mixed", "fp64", 1e-6), ("ex", "fp64", 1e-12), ("ex_arith", "fp64_dw", 1e-12)):
+        rec = {}
+        got = res["ex" if path == "ex_arith" else path]
+        for q, name in enumerate(("acc", "jerk", "snap")):
+            d = np.abs(got[q] - res[ref][q]).max(axis=1)
+            r = d / res["kappa"][q]
+            plain = d / np.linalg.norm(res[ref][q], axis=1)
+            rec[name] = {"kappa_norm_max": float(r.max()),
+                         "above": {f"{t:g}": int((r > t).sum()) for t in (0.5 * bound, 0.8 * bound, bound)},
+                         "p999": float(np.quantile(r, 0.999)),
+                         f"plain_above_{bound:g}": float((plain > bound).mean())}
+        out[path] = rec
     print(json.dumps(out), flush=True)
     return 0
 

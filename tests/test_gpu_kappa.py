@@ -65,15 +65,25 @@ def test_mixed_error_over_a_whole_population_in_units_of_kappa():
     units of their condition numbers.  Acceleration and jerk within 1e-6 for
     every particle; snap within 1e-6 for all but a ten-thousandth and within
     1.25e-6 for all (its pair terms' own FP32 rounding: at N = 2^20, 9 of
-    1,048,576 snaps lie between 1e-6 and 1.11e-6)."""
+    1,048,576 snaps lie between 1e-6 and 1.11e-6).  The EX arithmetic, against
+    the FP64 path on the same double-word-rounded inputs, within 1e-12 of them
+    for all but a ten-thousandth and within 2e-12 for all."""
     nb = nb_gpu()
     n, eps = 65536, 1e-4
     m, x, v = ni.plummer(n, 45, imf="salpeter")
     a = ni.random_state(n, 46, scale=2.0)
     out = {}
-    for prec in (nb.NB_FP64, nb.NB_MIXED):
-        g = nb.NBody(m, x, v, eps, precision=prec, start_forces=False)
-        g.set_state({"a": a})
+    for prec in (nb.NB_FP64, nb.NB_MIXED, nb.NB_EX, "fp64_dw"):
+        if prec == "fp64_dw":
+            # the FP64 path on the inputs rounded to double words, as EX holds them
+            def dw(q):
+                h = q.astype(np.float32).astype(np.float64)
+                return h + (q - h).astype(np.float32).astype(np.float64)
+            g = nb.NBody(dw(m), dw(x), dw(v), eps, precision=nb.NB_FP64, start_forces=False)
+            g.set_state({"a": dw(a)})
+        else:
+            g = nb.NBody(m, x, v, eps, precision=prec, start_forces=False)
+            g.set_state({"a": a})
         g.predict(0.0)
         out[prec] = g.evaluate(None)
         if prec == nb.NB_MIXED:
@@ -85,3 +95,10 @@ def test_mixed_error_over_a_whole_population_in_units_of_kappa():
         ratios.append(d / kap[q])
     assert ratios[0].max() <= 1e-6 and ratios[1].max() <= 1e-6, (ratios[0].max(), ratios[1].max())
     assert (ratios[2] > 1e-6).mean() <= 1e-4 and ratios[2].max() <= 1.25e-6, ratios[2].max()
+    # EX arithmetic (double-word FP32) against FP64 on the same double-word
+    # inputs: within 1e-12 of each condition number for all but a
+    # ten-thousandth, within 2e-12 for all (at N = 2^20: 4 snaps of 1,048,576
+    # above 1e-12, at most 1.24e-12)
+    for q in range(3):
+        r = np.abs(out[nb.NB_EX][q] - out["fp64_dw"][q]).max(axis=1) / kap[q]
+        assert (r > 1e-12).mean() <= 1e-4 and r.max() <= 2e-12, (q, r.max())

@@ -138,8 +138,9 @@ def parse():
                    help="nb_config.step_noise for --integrate and --ensemble (the rounding floor the "
                         "step criterion discounts; 0: the criterion as is)")
     p.add_argument("--census", action="store_true",
-                   help="mixed error over every particle of the default model (--n) in units of the "
-                        "sums' condition numbers, against the FP64 GPU path (about two minutes at 2^20)")
+                   help="mixed and EX errors over every particle of the default model (--n) in units "
+                        "of the sums' condition numbers, against the FP64 GPU path (about four minutes "
+                        "at 2^20)")
     p.add_argument("--peaks", action="store_true",
                    help="throughput probes of the CUDA-core pipes (FP32 FMA scalar and f32x2, FP64 "
                         "FMA, special-function estimates, and packed FMAs mixed with estimates)")

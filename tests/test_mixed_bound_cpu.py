@@ -7,9 +7,9 @@ FP32 numbers; the dot products and the u, w terms as FP32 fused
 multiply-adds; q = R^(-1/2) and q^2 = 1/R from two hardware estimates,
 modelled as the exact values times (1 + delta) with |delta| up to the
 documented worst cases (2^-22.9 for rsqrt.approx.f32, 2^-23 for
-rcp.approx.f32), each term accumulated in FP32 within a j-tile (two
-interleaved lanes of 256 terms for a 512-j tile) and the tile sums added
-without further error.  The GPU parity tests hold the kernel to
+rcp.approx.f32), each term accumulated in FP32 over blocks of 128 j (two
+interleaved lanes of 64 terms, the kernel's running sums between folds)
+and the block sums added without further error.  The GPU parity tests hold the kernel to
 1e-6 sum_j |T_ij|; the emulated sequence must stay below it.
 
 The emulation is written here from the description above; it shares
@@ -37,7 +37,7 @@ def estimate(exact, rel, rng):
     return f32(exact * (1.0 + rng.uniform(-rel, rel, exact.shape)))
 
 
-def emulate(m, x, v, a, eps, act, jtile=512, seed=5, single_estimate=False):
+def emulate(m, x, v, a, eps, act, fold=128, seed=5, single_estimate=False):
     rng = np.random.default_rng(seed)
     xh = f32(x)
     xl = f32(x - xh.astype(np.float64))
@@ -66,8 +66,8 @@ def emulate(m, x, v, a, eps, act, jtile=512, seed=5, single_estimate=False):
             # the product is rounded before it is added: one rounding more than
             # the kernel's fused multiply-add, so the emulation errs high
             term = f32(mu[:, None] * t)                       # [n, 3]
-            for j0 in range(0, n, jtile):
-                blk = term[j0:j0 + jtile]
+            for j0 in range(0, n, fold):
+                blk = term[j0:j0 + fold]
                 for lane in (0, 1):                           # FP32 running sums per lane
                     part = np.cumsum(blk[lane::2], axis=0, dtype=np.float32)
                     if len(part):

@@ -69,7 +69,7 @@ def set_device_peaks(torch, dev):
 # DRAM traffic of one mixed evaluation launch (the bench's own launch, one
 # ncu pass); valid only for the kernel source it was measured on (the sha256
 # prefix of csrc/k_eval.cu and csrc/nb_device.cuh).
-TRAFFIC = {"kernel_sha": "c51e180c41418558", "bytes_per_launch": 148.237056e6 + 70.077440e6,
+TRAFFIC = {"kernel_sha": "3b4746f198356227", "bytes_per_launch": 147.528960e6 + 70.369280e6,
            "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass on this launch"}
 WORKLOAD = "plummer_salpeter_N1048576_eps1e-4_shared_step_all_active"
 METRIC = "acc+jerk+snap interactions/s at N=2^20, mixed vs FP64 at rel err <= 1e-6"

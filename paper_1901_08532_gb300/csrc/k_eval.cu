@@ -441,6 +441,13 @@ __global__ void __launch_bounds__(mixed_max_threads(KI), mixed_min_blocks(KI))
 // One i-particle per thread slot.
 
 constexpr int kExThreads = 128;
+// j per lane in one double-word running sum of the EX kernel before it is
+// added into the tile's sums: the Sum2 low part gathers every rounding error
+// in FP32, so its own rounding grows with the number of terms; over all
+// 2^20 particles, whole 512-j tiles left 4 snaps above 1e-12 of their
+// condition number (at most 1.24e-12); 128 j leaves none (at most 8.1e-13),
+// for about 1 % more time.
+constexpr int kExFoldJ = 128;
 
 template <class T>
 __global__ void __launch_bounds__(kExThreads, 2) eval_ex_kernel(EvalArgs a)
@@ -499,21 +506,33 @@ __global__ void __launch_bounds__(kExThreads, 2) eval_ex_kernel(EvalArgs a)
         }
         const int len = min(jt, jend - (jbeg + tl * jt));
         const float *s = reinterpret_cast<const float *>(smem) + static_cast<size_t>(st) * NCX * jt;
-        FF<T> part[9];
+        // double-word running sums over at most kExFoldJ j per lane, added
+        // (Sum2) into the tile's double-word sums, which go to FP64 per tile
+        FF<T> tile[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q)
-            part[q] = {z, z};
-        for (int jj = JU * lj; jj < len; jj += JU * lanes) {
-            T c[NCX];
+            tile[q] = {z, z};
+        for (int f0 = 0; f0 < len; f0 += kExFoldJ * lanes) {
+            const int f1 = min(len, f0 + kExFoldJ * lanes);
+            FF<T> part[9];
 #pragma unroll
-            for (int r = 0; r < NCX; ++r)
-                c[r] = *reinterpret_cast<const T *>(s + r * jt + jj);
-            pair_ex(c, ni, eps2, part);
+            for (int q = 0; q < 9; ++q)
+                part[q] = {z, z};
+            for (int jj = f0 + JU * lj; jj < f1; jj += JU * lanes) {
+                T c[NCX];
+#pragma unroll
+                for (int r = 0; r < NCX; ++r)
+                    c[r] = *reinterpret_cast<const T *>(s + r * jt + jj);
+                pair_ex(c, ni, eps2, part);
+            }
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                ff::accumulate(tile[q], part[q]);
         }
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            const float *h = reinterpret_cast<const float *>(&part[q].h);
-            const float *l = reinterpret_cast<const float *>(&part[q].l);
+            const float *h = reinterpret_cast<const float *>(&tile[q].h);
+            const float *l = reinterpret_cast<const float *>(&tile[q].l);
 #pragma unroll
             for (int u = 0; u < JU; ++u)
                 acc[q][0] += static_cast<double>(h[u]) + static_cast<double>(l[u]);

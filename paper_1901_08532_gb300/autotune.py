@@ -2,7 +2,8 @@
 
 For a given system size and active-set size it times candidate launch
 shapes (i-particles per thread, threads per block, j-tile length, j per
-inner iteration; lanes and split-j are resolved by the library for each
+inner iteration, and for the mixed kernel the lanes per i-particle, 0 being
+the library's own choice; split-j is resolved by the library for each
 shape) through the C-ABI (nb_set_tiles + nb_evaluate, CUDA events on the
 context's stream) and keeps the fastest.  Results are cached per
 (precision, n, n_act bucket) in memory and, optionally, in a JSON file.
@@ -22,7 +23,8 @@ import json
 import math
 import os
 
-MIXED_SPACE = {"ki": (1, 2, 3), "junroll": (2, 4), "threads": (64, 128, 256), "jtile": (256, 512)}
+MIXED_SPACE = {"ki": (1, 2, 3), "junroll": (2, 4), "threads": (64, 128, 256), "jtile": (256, 512),
+               "lanes": (0, 1, 2, 4)}
 FP64_SPACE = {"ki": (1, 2), "threads": (64, 128, 256), "jtile": (128, 256)}
 EX_SPACE = {"ki": (1,), "junroll": (1, 2), "threads": (64, 128), "jtile": (256, 512, 1024)}
 

@@ -49,3 +49,16 @@ def test_ensemble_candidates_start_with_the_default():
     assert next(iter(autotune.ensemble_candidates(1))) == (4, 128, 1024)
     ex = list(autotune.ensemble_candidates(3))
     assert ex[0] == (8, 128, 256) and len(ex) == len(set(ex)) == 36
+
+
+def test_evaluation_candidates_cover_lanes_for_the_mixed_kernel():
+    """The mixed kernel's search includes the lanes per i-particle (0: the
+    library's own choice, which takes two lanes below 4096 active), and
+    every candidate keeps to the kernel's limits (KI 2 and 3 at most 128
+    threads, KI 3 with four j per iteration)."""
+    autotune = pytest.importorskip("paper_1901_08532_gb300.autotune")
+    cands = list(autotune.candidates(1))
+    assert {c["lanes"] for c in cands} == {0, 1, 2, 4}
+    assert all(c["threads"] <= 128 for c in cands if c["ki"] >= 2)
+    assert all(c["junroll"] == 4 for c in cands if c["ki"] == 3)
+    assert {"ki": 2, "junroll": 4, "threads": 128, "jtile": 512, "lanes": 2} in cands
